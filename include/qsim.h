@@ -1,0 +1,263 @@
+/*
+ * qsim.h -- C ABI of a GB300 (sm_103a) state-vector simulator for deep, fused
+ * gate streams with mid-circuit measurement.
+ *
+ * The method is the one of "Deep Quantum Circuit Simulations of Low-energy
+ * Nuclear States" (arXiv 2310.17739):
+ *   - state vector of 2^n complex amplitudes, qubit q = bit q of the index
+ *     (Section "State-Vector Simulation");
+ *   - gates applied by Eq. (1q-op) (2x2 on amplitude pairs) and Eq. (2q-op)
+ *     (4x4 on amplitude quadruples), the matrices need not be unitary;
+ *   - gate fusion (Section "Gate Fusion"): 1q+1q -> C1, 2q absorbs 1q forward
+ *     and backward -> C2, operand order canonicalised (first qubit lower),
+ *     2q+2q on one pair -> C2;
+ *   - mid-circuit measurement and its assertion variant (Section "Mid-Circuit
+ *     Measurement Assertion"): Born probability, outcome, collapse,
+ *     renormalisation; in assertion mode outcome 0 is asserted while P(0) > thr
+ *     and the product of the asserted P(0) is tracked.
+ *
+ * Conventions for every function:
+ *   - All functions return qsim_status; nothing throws or aborts across the ABI.
+ *   - A context is single-threaded: calls on one context must not overlap.
+ *     Different contexts may be used from different threads.
+ *   - Work is enqueued on the context's CUDA stream in call order.  Functions
+ *     that return results to host memory synchronise that stream; the others
+ *     return without waiting.  Errors raised by device work that was enqueued
+ *     earlier (a failed assertion, a CUDA fault) are reported by the next call
+ *     that synchronises.
+ *   - On an argument error (QSIM_E_INVAL) nothing is enqueued and the state is
+ *     unchanged.  A failed assertion (QSIM_E_ZEROPROB) leaves the state as it
+ *     was before that measurement and every later operation on the context is
+ *     skipped until qsim_reset_state or qsim_set_state.
+ *   - Pointers passed in are borrowed: gate, matrix and term arrays are fully
+ *     consumed (copied) before the call returns, so the caller may free or
+ *     reuse them immediately.
+ *   - qsim_last_error returns a message for the most recent failure.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QSIM_API __attribute__((visibility("default")))
+#else
+#define QSIM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsim_ctx qsim_ctx;
+typedef struct qsim_program qsim_program;
+
+typedef enum {
+    QSIM_C64 = 0,   /* complex64 amplitudes (float2), FP32 gate arithmetic,
+                       FP64 probability / norm / expectation / renormalisation */
+    QSIM_C128 = 1   /* complex128 amplitudes (double2), FP64 throughout */
+} qsim_dtype;
+
+typedef enum {
+    QSIM_OK = 0,
+    QSIM_E_INVAL = 1,     /* bad argument or malformed gate record */
+    QSIM_E_OOM = 2,       /* device or host allocation failed */
+    QSIM_E_CUDA = 3,      /* CUDA runtime error (message in qsim_last_error) */
+    QSIM_E_ZEROPROB = 4,  /* assertion-mode measurement with P(0) <= threshold */
+    QSIM_E_TIMEOUT = 5,   /* a bounded device wait expired */
+    QSIM_E_STATE = 6      /* context unusable after an earlier failure */
+} qsim_status;
+
+/* ---------------------------------------------------------------- records --
+ * One gate record (40 bytes).  q0 is the first operand: the control of
+ * controlled gates.  For 2-qubit matrices the local basis index is
+ * l = b_q0 + 2*b_q1 (row-major 4x4, rows = output).  C1 and C2 carry a general
+ * (not necessarily unitary) 2x2 / 4x4 complex matrix at mats[mat ...]:
+ * 8 / 32 doubles, interleaved (re, im), row-major.  Angles are in p[].
+ * Gate definitions: the OpenQASM gate table of the paper (Table "Gates defined
+ * in IBM OpenQASM") with RX/RY/RZ(t) = exp(-i t {X,Y,Z}/2), U1(l) = diag(1, e^{il}),
+ * U2(p,l) = U3(pi/2,p,l), U3(t,p,l) = [[cos t/2, -e^{il} sin t/2],
+ * [e^{ip} sin t/2, e^{i(p+l)} cos t/2]], CU1/CU3/CRX/CRY/CRZ/CY/CH controlled
+ * versions, RXX/RZZ(t) = exp(-i t XX/2), exp(-i t ZZ/2).
+ * MEASURE q0: flags bit 0 set = assertion mode (outcome 0 asserted).
+ * RESET q0: a drawn measurement, then the |1> half moved onto |0>.
+ * BARRIER: no effect on the state; stops fusion and reordering across it.
+ */
+typedef struct {
+    uint16_t op;
+    uint16_t flags;
+    uint32_t q0;
+    uint32_t q1;
+    uint32_t mat;
+    double p[3];
+} qsim_gate;
+
+enum {
+    QSIM_OP_ID = 0, QSIM_OP_X = 1, QSIM_OP_Y = 2, QSIM_OP_Z = 3, QSIM_OP_H = 4,
+    QSIM_OP_S = 5, QSIM_OP_SDG = 6, QSIM_OP_T = 7, QSIM_OP_TDG = 8,
+    QSIM_OP_RX = 9, QSIM_OP_RY = 10, QSIM_OP_RZ = 11, QSIM_OP_U1 = 12,
+    QSIM_OP_U2 = 13, QSIM_OP_U3 = 14, QSIM_OP_C1 = 15,
+    QSIM_OP_CX = 32, QSIM_OP_CY = 33, QSIM_OP_CZ = 34, QSIM_OP_CH = 35,
+    QSIM_OP_SWAP = 36, QSIM_OP_CRX = 37, QSIM_OP_CRY = 38, QSIM_OP_CRZ = 39,
+    QSIM_OP_CU1 = 40, QSIM_OP_CU3 = 41, QSIM_OP_RXX = 42, QSIM_OP_RZZ = 43,
+    QSIM_OP_C2 = 44,
+    QSIM_OP_MEASURE = 64, QSIM_OP_RESET = 65, QSIM_OP_BARRIER = 66
+};
+
+#define QSIM_MEAS_ASSERT 1u
+
+/* Pauli string: bit q of x_mask = X or Y on qubit q, bit q of z_mask = Z or Y. */
+typedef struct {
+    uint64_t x_mask;
+    uint64_t z_mask;
+    double coef;
+} qsim_pauli_term;
+
+/* ------------------------------------------------------------- compiling --
+ * fusion   0: no fusion (one C1/C2 op per gate, still tiled into passes);
+ *          1: the paper's four fusion stages (C1/C2 only).
+ * k_max    2: the paper's C1/C2 ops; 3..5: fused ops of a pass are further
+ *          merged into dense 2^k x 2^k blocks of up to k_max qubits when the
+ *          cost model says it is cheaper.
+ * tile_bits m: qubits per shared-memory tile (pass); 0 picks by dtype and n.
+ *          States with n <= tile limit run resident in one block.
+ * threads  threads per block; 0 = 256.
+ * chunk_gates  qsim_apply compiles and launches the stream in chunks of this
+ *          many gates, overlapping host compilation with device work; 0 = 2^20.
+ * lookahead  how many fused ops the pass scheduler may scan past an op that
+ *          does not fit, pulling later ops on disjoint qubits forward; 0 = 64.
+ * compile_threads  host threads compiling chunks ahead of the launcher; 0 = auto.
+ */
+typedef struct {
+    int32_t fusion;
+    int32_t k_max;
+    int32_t tile_bits;
+    int32_t threads;
+    int32_t chunk_gates;
+    int32_t lookahead;
+    int32_t compile_threads;
+    int32_t reserved;
+} qsim_config;
+
+typedef struct {
+    uint64_t gates;          /* input records */
+    uint64_t fused_ops;      /* dense ops after fusion (C1/C2/k-blocks) */
+    uint64_t passes;         /* full-state sweeps of dense ops */
+    uint64_t measurements;   /* MEASURE and RESET records */
+    uint64_t device_bytes;   /* device memory held by a compiled program */
+    uint64_t op_hist[8];     /* fused ops by qubit count k (index k) */
+} qsim_program_info;
+
+/* Allocator hook: alloc(bytes, stream, user) -> device pointer or NULL;
+ * free(ptr, bytes, stream, user).  Frees are stream-ordered on `stream`. */
+typedef void *(*qsim_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*qsim_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* ------------------------------------------------------------- lifecycle -- */
+
+/* New context holding a 2^n-amplitude state |0...0> on the current CUDA
+ * device, enqueued on `stream` (NULL = legacy default stream).  Device memory
+ * comes from alloc/free when given (both or neither), else cudaMallocAsync.
+ * 1 <= n_qubits <= 34.  QSIM_E_OOM when the state does not fit. */
+QSIM_API qsim_status qsim_create(int n_qubits, qsim_dtype dtype, void *stream,
+                        qsim_alloc_fn alloc, qsim_free_fn free_fn, void *user,
+                        qsim_ctx **out);
+/* Releases the state and every buffer of the context (stream-ordered). */
+QSIM_API qsim_status qsim_destroy(qsim_ctx *ctx);
+QSIM_API qsim_status qsim_set_stream(qsim_ctx *ctx, void *stream);
+QSIM_API qsim_status qsim_set_config(qsim_ctx *ctx, const qsim_config *cfg);
+QSIM_API qsim_status qsim_get_config(const qsim_ctx *ctx, qsim_config *cfg);
+/* Seed of the draws of in-stream MEASURE/RESET records (default 0). */
+QSIM_API qsim_status qsim_set_seed(qsim_ctx *ctx, uint64_t seed);
+/* Assertion-mode threshold: fail when P(0) <= thr (default 0, as in the paper). */
+QSIM_API qsim_status qsim_set_assert_threshold(qsim_ctx *ctx, double thr);
+
+/* ------------------------------------------------------- gate application --
+ * Eq. (1q-op)/(2q-op) over a gate stream, after the fusion of Section "Gate
+ * Fusion" and tiling into shared-memory passes.  Asynchronous.  Each MEASURE /
+ * RESET record consumes the next draw ordinal k of the context and draws
+ * u(seed, k) with the context seed. */
+QSIM_API qsim_status qsim_apply(qsim_ctx *ctx, const qsim_gate *gates, size_t n_gates,
+                       const double *mats, size_t n_mats);
+/* Compile once into a device-resident program; run it any number of times.
+ * The program belongs to the context that compiled it (same n and dtype). */
+QSIM_API qsim_status qsim_compile(qsim_ctx *ctx, const qsim_gate *gates, size_t n_gates,
+                         const double *mats, size_t n_mats, qsim_program **out);
+QSIM_API qsim_status qsim_run(qsim_ctx *ctx, const qsim_program *prog);
+QSIM_API qsim_status qsim_program_get_info(const qsim_program *prog, qsim_program_info *info);
+QSIM_API qsim_status qsim_program_free(qsim_program *prog);
+
+/* ------------------------------------------------------------ measurement --
+ * Section "Mid-Circuit Measurement Assertion".  p0 = sum |a_i|^2 over bit q = 0,
+ * p1 likewise (FP64).  mode 0: outcome 0 iff u(seed, k) < p0/(p0+p1), with
+ * u(seed, k) = (word 0 of Philox4x64-10, counter (k,0,0,0), key (seed,0)) >> 11
+ * times 2^-53 and k the context's next draw ordinal.  mode 1 (assertion):
+ * outcome 0 when p0/(p0+p1) > thr, else QSIM_E_ZEROPROB with the state kept.
+ * Then amplitudes with bit q != outcome are zeroed and the rest scaled by
+ * 1/sqrt(p_outcome) (FP64 scale).  *prob = p_outcome/(p0+p1).  When outcome
+ * is non-NULL the call synchronises and returns the result; when it is NULL
+ * the measurement stays asynchronous (read it later with qsim_outcomes). */
+QSIM_API qsim_status qsim_measure(qsim_ctx *ctx, int qubit, uint64_t seed, int mode,
+                         int *outcome, double *prob);
+/* Born probabilities of one qubit without collapsing (synchronises). */
+QSIM_API qsim_status qsim_prob(qsim_ctx *ctx, int qubit, double *p0, double *p1);
+/* Outcome log of every measurement since the last reset, in order:
+ * outcomes[i] in {0, 1} (-1 = failed assertion), probs[i] = probability of the
+ * recorded outcome.  Synchronises.  *n_total = records available. */
+QSIM_API qsim_status qsim_outcomes(qsim_ctx *ctx, int32_t *outcomes, double *probs, size_t cap,
+                          size_t *n_total);
+/* Product of the asserted P(0) since the last reset (1 if none).  Synchronises. */
+QSIM_API qsim_status qsim_success_prob(qsim_ctx *ctx, double *p);
+
+/* ------------------------------------------------------------ expectation --
+ * out[t] = coef_t * Re <psi| P_t |psi> with P_t |j> = i^{#Y} (-1)^{popcount(j & z)}
+ * |j ^ x>, FP64 accumulation, for t < n_terms.  Synchronises. */
+QSIM_API qsim_status qsim_expect(qsim_ctx *ctx, const qsim_pauli_term *terms, size_t n_terms,
+                        double *out);
+
+/* ------------------------------------------------------------------ state --
+ * Copy the 2^n amplitudes out / in (bytes must equal 2^n * 8 for C64 or
+ * 2^n * 16 for C128; interleaved re, im).  dst/src may be device or host.
+ * qsim_state synchronises.  qsim_reset_state restores |0...0> and clears the
+ * draw ordinal, the outcome log, the success product and a failed-assertion
+ * mark. */
+QSIM_API qsim_status qsim_state(qsim_ctx *ctx, void *dst, size_t bytes, int dst_is_device);
+QSIM_API qsim_status qsim_set_state(qsim_ctx *ctx, const void *src, size_t bytes, int src_is_device);
+QSIM_API qsim_status qsim_reset_state(qsim_ctx *ctx);
+/* Device pointer of the state (valid until qsim_destroy) and its size. */
+QSIM_API qsim_status qsim_state_ptr(qsim_ctx *ctx, void **dptr, size_t *bytes);
+/* Wait for all enqueued work; report deferred device errors. */
+QSIM_API qsim_status qsim_sync(qsim_ctx *ctx);
+QSIM_API const char *qsim_last_error(const qsim_ctx *ctx);
+QSIM_API const char *qsim_status_string(qsim_status s);
+
+/* ------------------------------------------- host-only compiler inspection --
+ * These run the host compiler only (no GPU needed).
+ *
+ * qsim_fuse: the fusion stages of Section "Gate Fusion", the pass schedule
+ * and (for k_max > 2) the k-qubit merge over gates[0..n_gates), exactly as
+ * qsim_apply compiles one chunk.  Writes the fused ops in execution order:
+ * out_k[i] = qubit count (1..5) or 0 for a MEASURE/RESET record
+ * (then out_q[6i] = qubit, out_q[6i+1] = op code, out_q[6i+2] = flags);
+ * out_q[6i .. 6i+k) = qubits, with bit j of the local matrix index = qubit
+ * out_q[6i+j]; the 2^k x 2^k row-major complex matrix (interleaved doubles)
+ * starts at out_mats[out_mat[i]].  Returns QSIM_E_INVAL when a capacity is too
+ * small (*n_ops / *n_mat_doubles then give the sizes needed). */
+QSIM_API qsim_status qsim_fuse(int n_qubits, qsim_dtype dtype, const qsim_gate *gates, size_t n_gates,
+                      const double *mats, size_t n_mats, const qsim_config *cfg,
+                      uint8_t *out_k, uint32_t *out_q, uint64_t *out_mat, size_t cap_ops,
+                      double *out_mats, size_t cap_mat_doubles,
+                      size_t *n_ops, size_t *n_mat_doubles);
+/* qsim_schedule: the pass schedule of the same compile.  For pass i:
+ * out_tile[i] = bit mask of the tile qubits (0 for a measurement pass),
+ * out_first[i], out_count[i] = its range in the op order qsim_fuse returns. */
+QSIM_API qsim_status qsim_schedule(int n_qubits, qsim_dtype dtype, const qsim_gate *gates, size_t n_gates,
+                          const double *mats, size_t n_mats, const qsim_config *cfg,
+                          uint64_t *out_tile, uint64_t *out_first, uint32_t *out_count,
+                          size_t cap, size_t *n_passes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

@@ -1,0 +1,849 @@
+// capi.cpp -- the C ABI of include/qsim.h: contexts, device buffers, program
+// upload, launch sequencing, and the pipelined compile-and-launch of qsim_apply
+// (host threads compile chunks of the gate stream while earlier chunks run).
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qsim.h"
+#include "compiler.h"
+#include "kernels.h"
+
+using qsim::cd;
+using qsim::Config;
+using qsim::DevOp;
+using qsim::HostProgram;
+using qsim::MeasCtl;
+using qsim::MeasRec;
+using qsim::Pass;
+
+namespace {
+
+// Host image of one compiled chunk, ready for upload: DevOps + matrices in the
+// state's dtype, plus the pass list the launcher walks.
+struct Packed {
+    std::vector<DevOp> ops;
+    std::vector<unsigned char> mats;
+    std::vector<Pass> passes;
+    int n = 0, m = 0;
+    bool resident = false;
+    uint64_t gates = 0, measurements = 0, fused = 0, dense_passes = 0;
+    uint64_t hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// Device image of one compiled chunk.
+struct DevChunk {
+    DevOp *d_ops = nullptr;
+    size_t n_ops = 0;
+    void *d_mats = nullptr;
+    size_t mats_bytes = 0;
+    std::vector<Pass> passes;
+    int m = 0;
+    bool resident = false;
+    uint64_t measurements = 0;
+};
+
+void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
+    pk.n = hp.n;
+    pk.m = hp.m;
+    pk.resident = hp.resident;
+    pk.gates = hp.gates;
+    pk.measurements = hp.measurements;
+    std::memcpy(pk.hist, hp.hist, sizeof(pk.hist));
+    pk.ops.resize(hp.ops.size());
+    const size_t es = dt == QSIM_C64 ? 8 : 16;
+    pk.mats.resize(hp.pool.size() * es);
+    if (dt == QSIM_C64) {
+        float *f = reinterpret_cast<float *>(pk.mats.data());
+        for (size_t i = 0; i < hp.pool.size(); i++) {
+            f[2 * i] = (float)hp.pool[i].real();
+            f[2 * i + 1] = (float)hp.pool[i].imag();
+        }
+    } else if (!hp.pool.empty()) {
+        std::memcpy(pk.mats.data(), hp.pool.data(), hp.pool.size() * 16);
+    }
+    pk.passes = hp.passes;
+    uint64_t fused = 0, dp = 0;
+    for (const Pass &p : hp.passes) {
+        if (p.ev) {
+            const qsim::FOp &o = hp.ops[p.first];
+            DevOp &d = pk.ops[p.first];
+            std::memset(&d, 0, sizeof(d));
+            d.ev = o.ev;
+            d.flags = o.flags;
+            d.lq[0] = (uint8_t)o.q[0];
+            continue;
+        }
+        dp++;
+        for (uint64_t i = p.first; i < p.first + p.count; i++) {
+            const qsim::FOp &o = hp.ops[i];
+            DevOp &d = pk.ops[i];
+            std::memset(&d, 0, sizeof(d));
+            d.k = o.k;
+            for (int j = 0; j < o.k; j++)
+                d.lq[j] = (uint8_t)__builtin_popcountll(p.tile & ((1ull << o.q[j]) - 1ull));
+            d.mat = (uint32_t)o.mat;
+            fused++;
+        }
+    }
+    pk.fused = fused;
+    pk.dense_passes = dp;
+}
+
+struct Staging {
+    void *host = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+};
+
+thread_local std::string g_err;
+
+}  // namespace
+
+struct qsim_ctx {
+    int n = 0;
+    qsim_dtype dtype = QSIM_C64;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    qsim_alloc_fn alloc = nullptr;
+    qsim_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    void *state = nullptr;
+    size_t state_bytes = 0;
+    MeasCtl *ctl = nullptr;
+    MeasRec *log = nullptr;
+    size_t log_cap = 0;
+    uint64_t log_n = 0;
+    double *partials = nullptr;
+    size_t partials_cap = 0;  // doubles
+    uint64_t ordinal = 0;
+    uint64_t seed = 0;
+    double thr = 0.0;
+    Config cfg;
+    MeasCtl *h_ctl = nullptr;  // pinned readback of the control block
+    std::vector<Staging> staging;
+    std::string err;
+    bool broken = false;
+};
+
+struct qsim_program {
+    qsim_ctx *owner = nullptr;
+    std::vector<DevChunk> chunks;
+    qsim_program_info info{};
+};
+
+namespace {
+
+qsim_status fail(qsim_ctx *c, qsim_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    g_err = msg;
+    return s;
+}
+
+qsim_status cuda_fail(qsim_ctx *c, cudaError_t e, const char *what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (c) c->broken = true;
+    return fail(c, QSIM_E_CUDA, msg);
+}
+
+#define CK(expr, what)                                         \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what);  \
+    } while (0)
+
+void *dalloc(qsim_ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c->alloc) return c->alloc(bytes, c->stream, c->user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(qsim_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, bytes, c->stream, c->user);
+    else cudaFreeAsync(p, c->stream);
+}
+
+// A pinned staging buffer whose previous copy has completed.
+Staging *get_staging(qsim_ctx *c, size_t bytes) {
+    for (auto &s : c->staging)
+        if (s.bytes >= bytes && cudaEventQuery(s.done) == cudaSuccess) return &s;
+    cudaGetLastError();
+    if (c->staging.size() >= 8) {  // bound pinned memory: wait for the oldest fitting one
+        for (auto &s : c->staging)
+            if (s.bytes >= bytes) {
+                cudaEventSynchronize(s.done);
+                return &s;
+            }
+    }
+    Staging s;
+    s.bytes = std::max(bytes, (size_t)1 << 22);
+    if (cudaHostAlloc(&s.host, s.bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeHost(s.host);
+        cudaGetLastError();
+        return nullptr;
+    }
+    c->staging.push_back(s);
+    return &c->staging.back();
+}
+
+// Stream-ordered upload of host bytes through a pinned staging buffer.
+qsim_status upload(qsim_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return QSIM_OK;
+    Staging *s = get_staging(c, bytes);
+    if (!s) return fail(c, QSIM_E_OOM, "pinned staging allocation failed");
+    std::memcpy(s->host, src, bytes);
+    CK(cudaMemcpyAsync(dst, s->host, bytes, cudaMemcpyHostToDevice, c->stream), "upload");
+    CK(cudaEventRecord(s->done, c->stream), "upload event");
+    return QSIM_OK;
+}
+
+qsim_status ensure_log(qsim_ctx *c, uint64_t need) {
+    if (need <= c->log_cap) return QSIM_OK;
+    size_t cap = std::max<size_t>(c->log_cap * 2, 1024);
+    while (cap < need) cap *= 2;
+    MeasRec *nl = (MeasRec *)dalloc(c, cap * sizeof(MeasRec));
+    if (!nl) return fail(c, QSIM_E_OOM, "measurement log allocation failed");
+    if (c->log) {
+        CK(cudaMemcpyAsync(nl, c->log, c->log_cap * sizeof(MeasRec), cudaMemcpyDeviceToDevice,
+                           c->stream),
+           "log grow");
+        dfree(c, c->log, c->log_cap * sizeof(MeasRec));
+    }
+    c->log = nl;
+    c->log_cap = cap;
+    return QSIM_OK;
+}
+
+qsim_status ensure_partials(qsim_ctx *c, size_t doubles) {
+    if (doubles <= c->partials_cap) return QSIM_OK;
+    size_t cap = std::max<size_t>(c->partials_cap * 2, 4096);
+    while (cap < doubles) cap *= 2;
+    double *p = (double *)dalloc(c, cap * sizeof(double));
+    if (!p) return fail(c, QSIM_E_OOM, "reduction scratch allocation failed");
+    dfree(c, c->partials, c->partials_cap * sizeof(double));
+    c->partials = p;
+    c->partials_cap = cap;
+    return QSIM_OK;
+}
+
+qsim_status check_usable(qsim_ctx *c) {
+    if (!c) return fail(nullptr, QSIM_E_INVAL, "null context");
+    if (c->broken) return fail(c, QSIM_E_STATE, "context unusable after an earlier CUDA error");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return QSIM_OK;
+}
+
+// Synchronise, read the control block, report deferred device failures.
+qsim_status sync_read(qsim_ctx *c) {
+    CK(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(MeasCtl), cudaMemcpyDeviceToHost, c->stream),
+       "control readback");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (c->h_ctl->status == QSIM_E_ZEROPROB)
+        return fail(c, QSIM_E_ZEROPROB,
+                    "assertion-mode measurement #" + std::to_string(c->h_ctl->fail_log) +
+                        " found P(0) <= threshold; later operations were skipped");
+    return QSIM_OK;
+}
+
+qsim_status upload_chunk(qsim_ctx *c, const Packed &pk, DevChunk &dc) {
+    dc.n_ops = pk.ops.size();
+    dc.mats_bytes = pk.mats.size();
+    dc.passes = pk.passes;
+    dc.m = pk.m;
+    dc.resident = pk.resident;
+    dc.measurements = pk.measurements;
+    dc.d_ops = (DevOp *)dalloc(c, std::max<size_t>(dc.n_ops, 1) * sizeof(DevOp));
+    dc.d_mats = dalloc(c, std::max<size_t>(dc.mats_bytes, 16));
+    if (!dc.d_ops || !dc.d_mats) {
+        dfree(c, dc.d_ops, 0);
+        dfree(c, dc.d_mats, 0);
+        dc.d_ops = nullptr;
+        dc.d_mats = nullptr;
+        return fail(c, QSIM_E_OOM, "program allocation failed");
+    }
+    qsim_status s = upload(c, dc.d_ops, pk.ops.data(), dc.n_ops * sizeof(DevOp));
+    if (s == QSIM_OK) s = upload(c, dc.d_mats, pk.mats.data(), dc.mats_bytes);
+    return s;
+}
+
+void release_chunk(qsim_ctx *c, DevChunk &dc) {
+    dfree(c, dc.d_ops, dc.n_ops * sizeof(DevOp));
+    dfree(c, dc.d_mats, dc.mats_bytes);
+    dc.d_ops = nullptr;
+    dc.d_mats = nullptr;
+}
+
+qsim_status launch_measure(qsim_ctx *c, int q, int mode, int reset, uint64_t seed) {
+    qsim_status s = ensure_log(c, c->log_n + 1);
+    if (s != QSIM_OK) return s;
+    s = ensure_partials(c, 2 * (size_t)qsim::prob_blocks(c->n));
+    if (s != QSIM_OK) return s;
+    qsim::MeasArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.q = q;
+    a.mode = mode;
+    a.reset = reset;
+    a.seed = seed;
+    a.ordinal = c->ordinal;
+    a.log_idx = c->log_n;
+    a.log_cap = c->log_cap;
+    a.thr = c->thr;
+    CK(qsim::launch_measure(c->dtype, c->state, c->n, a, c->partials, c->ctl, c->log, c->stream),
+       "measure launch");
+    c->ordinal++;
+    c->log_n++;
+    return QSIM_OK;
+}
+
+qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
+    const int threads = c->cfg.threads == 512 ? 512 : 256;
+    if (dc.resident) {
+        qsim_status s = ensure_log(c, c->log_n + dc.measurements);
+        if (s != QSIM_OK) return s;
+        qsim::Instance in;
+        std::memset(&in, 0, sizeof(in));
+        in.state = c->state;
+        in.ops = dc.d_ops;
+        in.mats = dc.d_mats;
+        in.n_ops = dc.n_ops;
+        in.seed = c->seed;
+        in.ordinal0 = c->ordinal;
+        in.log0 = c->log_n;
+        in.log_cap = c->log_cap;
+        in.ctl = c->ctl;
+        in.log = c->log;
+        in.thr = c->thr;
+        in.n = c->n;
+        if (dc.n_ops) CK(qsim::launch_resident(c->dtype, threads, in, c->stream), "resident launch");
+        c->ordinal += dc.measurements;
+        c->log_n += dc.measurements;
+        return QSIM_OK;
+    }
+    for (const Pass &p : dc.passes) {
+        if (p.ev) {
+            qsim_status s = launch_measure(c, (int)p.q, p.flags, p.ev == qsim::EV_RESET, c->seed);
+            if (s != QSIM_OK) return s;
+            continue;
+        }
+        if (!p.count) continue;
+        CK(qsim::launch_tile_pass(c->dtype, threads, c->state, c->n, dc.m, p.tile,
+                                  dc.d_ops + p.first, p.count, dc.d_mats, c->ctl, c->stream),
+           "tile pass launch");
+    }
+    return QSIM_OK;
+}
+
+size_t chunk_size(const qsim_ctx *c) {
+    return c->cfg.chunk_gates > 0 ? (size_t)c->cfg.chunk_gates : ((size_t)1 << 20);
+}
+
+int compile_threads(const qsim_ctx *c) {
+    if (c->cfg.compile_threads > 0) return c->cfg.compile_threads;
+    unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(h > 1 ? h - 1 : 1u, 32u));
+}
+
+// Compile chunks [0, nchunks) on worker threads and hand them, in order, to
+// `sink`.  At most `ahead` chunks are compiled but not yet consumed.
+template <class Sink>
+qsim_status compile_chunks(qsim_ctx *c, const qsim_gate *g, size_t ng, const double *mats,
+                           size_t nm, Sink sink) {
+    const size_t C = chunk_size(c);
+    const size_t nchunks = ng ? (ng + C - 1) / C : 0;
+    if (nchunks <= 1) {
+        HostProgram hp;
+        qsim::compile(c->n, c->dtype, c->cfg, g, ng, mats, nm, hp);
+        Packed pk;
+        pack(hp, c->dtype, pk);
+        return sink(pk);
+    }
+    const int T = std::min<int>(compile_threads(c), (int)nchunks);
+    const size_t ahead = (size_t)T * 2;
+    std::vector<std::unique_ptr<Packed>> slots(nchunks);
+    std::mutex mu;
+    std::condition_variable cv;
+    std::atomic<size_t> next{0};
+    size_t consumed = 0;
+    bool stop = false;
+    auto worker = [&]() {
+        for (;;) {
+            size_t i;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || next.load() < consumed + ahead || next.load() >= nchunks; });
+                if (stop || next.load() >= nchunks) return;
+                i = next++;
+            }
+            const size_t b = i * C, e = std::min(ng, b + C);
+            HostProgram hp;
+            qsim::compile(c->n, c->dtype, c->cfg, g + b, e - b, mats, nm, hp);
+            auto pk = std::make_unique<Packed>();
+            pack(hp, c->dtype, *pk);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                slots[i] = std::move(pk);
+            }
+            cv.notify_all();
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; t++) th.emplace_back(worker);
+    qsim_status st = QSIM_OK;
+    for (size_t i = 0; i < nchunks; i++) {
+        std::unique_ptr<Packed> pk;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] { return slots[i] != nullptr; });
+            pk = std::move(slots[i]);
+            consumed = i + 1;
+        }
+        cv.notify_all();
+        st = sink(*pk);
+        if (st != QSIM_OK) break;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        stop = true;
+    }
+    cv.notify_all();
+    for (auto &t : th) t.join();
+    return st;
+}
+
+void accumulate(qsim_program_info &info, const Packed &pk, size_t dev_bytes) {
+    info.gates += pk.gates;
+    info.fused_ops += pk.fused;
+    info.passes += pk.dense_passes;
+    info.measurements += pk.measurements;
+    info.device_bytes += dev_bytes;
+    for (int k = 0; k < 8; k++) info.op_hist[k] += pk.hist[k];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qsim_status_string(qsim_status s) {
+    switch (s) {
+        case QSIM_OK: return "ok";
+        case QSIM_E_INVAL: return "invalid argument";
+        case QSIM_E_OOM: return "out of memory";
+        case QSIM_E_CUDA: return "CUDA error";
+        case QSIM_E_ZEROPROB: return "assertion failed: P(0) <= threshold";
+        case QSIM_E_TIMEOUT: return "timeout";
+        case QSIM_E_STATE: return "context unusable";
+    }
+    return "unknown status";
+}
+
+const char *qsim_last_error(const qsim_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+qsim_status qsim_create(int n, qsim_dtype dtype, void *stream, qsim_alloc_fn alloc,
+                        qsim_free_fn free_fn, void *user, qsim_ctx **out) {
+    if (!out) return fail(nullptr, QSIM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 34) return fail(nullptr, QSIM_E_INVAL, "n_qubits must be in [1, 34]");
+    if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(nullptr, QSIM_E_INVAL, "bad dtype");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(nullptr, QSIM_E_INVAL, "alloc and free must be given together");
+    static std::once_flag once;
+    static cudaError_t setup_err = cudaSuccess;
+    std::call_once(once, [] { setup_err = qsim::setup_kernels(); });
+    if (setup_err != cudaSuccess)
+        return fail(nullptr, QSIM_E_CUDA, std::string("kernel setup: ") + cudaGetErrorString(setup_err));
+    auto c = std::make_unique<qsim_ctx>();
+    c->n = n;
+    c->dtype = dtype;
+    c->stream = (cudaStream_t)stream;
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = user;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, QSIM_E_CUDA, "no CUDA device");
+    }
+    c->state_bytes = (size_t)(dtype == QSIM_C64 ? 8 : 16) << n;
+    c->state = dalloc(c.get(), c->state_bytes);
+    if (!c->state) return fail(nullptr, QSIM_E_OOM, "state allocation failed");
+    c->ctl = (MeasCtl *)dalloc(c.get(), sizeof(MeasCtl));
+    if (cudaMallocHost((void **)&c->h_ctl, sizeof(MeasCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_ctl = nullptr;
+    }
+    if (!c->ctl || !c->h_ctl) {
+        dfree(c.get(), c->state, c->state_bytes);
+        dfree(c.get(), c->ctl, sizeof(MeasCtl));
+        if (c->h_ctl) cudaFreeHost(c->h_ctl);
+        return fail(nullptr, QSIM_E_OOM, "control block allocation failed");
+    }
+    qsim_status s = qsim_reset_state(c.get());
+    if (s != QSIM_OK) {
+        qsim_destroy(c.release());
+        return s;
+    }
+    *out = c.release();
+    return QSIM_OK;
+}
+
+qsim_status qsim_destroy(qsim_ctx *c) {
+    if (!c) return QSIM_OK;
+    cudaSetDevice(c->device);
+    dfree(c, c->state, c->state_bytes);
+    dfree(c, c->ctl, sizeof(MeasCtl));
+    dfree(c, c->log, c->log_cap * sizeof(MeasRec));
+    dfree(c, c->partials, c->partials_cap * sizeof(double));
+    cudaStreamSynchronize(c->stream);
+    for (auto &s : c->staging) {
+        cudaEventDestroy(s.done);
+        cudaFreeHost(s.host);
+    }
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    cudaGetLastError();
+    delete c;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_stream(qsim_ctx *c, void *stream) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    // order the new stream after everything enqueued on the old one
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    c->stream = (cudaStream_t)stream;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_config(qsim_ctx *c, const qsim_config *cfg) {
+    if (!c || !cfg) return fail(c, QSIM_E_INVAL, "null argument");
+    if (cfg->fusion < 0 || cfg->fusion > 1) return fail(c, QSIM_E_INVAL, "fusion must be 0 or 1");
+    if (cfg->k_max != 0 && (cfg->k_max < 2 || cfg->k_max > 5))
+        return fail(c, QSIM_E_INVAL, "k_max must be 0 or in [2, 5]");
+    const int mx = qsim::max_resident_bits(c->dtype);
+    if (cfg->tile_bits < 0 || cfg->tile_bits > mx)
+        return fail(c, QSIM_E_INVAL, "tile_bits out of range for this dtype");
+    if (cfg->tile_bits > 0 && cfg->tile_bits < c->n && cfg->tile_bits < 6)
+        return fail(c, QSIM_E_INVAL, "tile_bits must be >= 6 unless it covers the whole state");
+    if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
+        return fail(c, QSIM_E_INVAL, "threads must be 0, 256 or 512");
+    if (cfg->chunk_gates < 0 || cfg->lookahead < 0 || cfg->compile_threads < 0)
+        return fail(c, QSIM_E_INVAL, "negative size");
+    c->cfg = qsim::config_from(cfg);
+    return QSIM_OK;
+}
+
+qsim_status qsim_get_config(const qsim_ctx *c, qsim_config *cfg) {
+    if (!c || !cfg) return QSIM_E_INVAL;
+    qsim::config_to(c->cfg, cfg);
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_seed(qsim_ctx *c, uint64_t seed) {
+    if (!c) return fail(nullptr, QSIM_E_INVAL, "null context");
+    c->seed = seed;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_assert_threshold(qsim_ctx *c, double thr) {
+    if (!c) return fail(nullptr, QSIM_E_INVAL, "null context");
+    if (!(thr >= 0.0 && thr < 1.0)) return fail(c, QSIM_E_INVAL, "threshold must be in [0, 1)");
+    c->thr = thr;
+    return QSIM_OK;
+}
+
+qsim_status qsim_apply(qsim_ctx *c, const qsim_gate *g, size_t ng, const double *mats, size_t nm) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (ng && !g) return fail(c, QSIM_E_INVAL, "gates is NULL");
+    std::string err;
+    if (!qsim::validate(c->n, g, ng, mats, nm, err)) return fail(c, QSIM_E_INVAL, err);
+    return compile_chunks(c, g, ng, mats, nm, [&](const Packed &pk) -> qsim_status {
+        DevChunk dc;
+        qsim_status st = upload_chunk(c, pk, dc);
+        if (st == QSIM_OK) st = launch_chunk(c, dc);
+        release_chunk(c, dc);  // stream-ordered: freed after the launches above
+        return st;
+    });
+}
+
+qsim_status qsim_compile(qsim_ctx *c, const qsim_gate *g, size_t ng, const double *mats, size_t nm,
+                         qsim_program **out) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (!out) return fail(c, QSIM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (ng && !g) return fail(c, QSIM_E_INVAL, "gates is NULL");
+    std::string err;
+    if (!qsim::validate(c->n, g, ng, mats, nm, err)) return fail(c, QSIM_E_INVAL, err);
+    auto prog = std::make_unique<qsim_program>();
+    prog->owner = c;
+    s = compile_chunks(c, g, ng, mats, nm, [&](const Packed &pk) -> qsim_status {
+        DevChunk dc;
+        qsim_status st = upload_chunk(c, pk, dc);
+        if (st != QSIM_OK) {
+            release_chunk(c, dc);
+            return st;
+        }
+        accumulate(prog->info, pk, dc.n_ops * sizeof(DevOp) + dc.mats_bytes);
+        prog->chunks.push_back(std::move(dc));
+        return QSIM_OK;
+    });
+    if (s != QSIM_OK) {
+        qsim_program_free(prog.release());
+        return s;
+    }
+    *out = prog.release();
+    return QSIM_OK;
+}
+
+qsim_status qsim_run(qsim_ctx *c, const qsim_program *p) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (!p || p->owner != c) return fail(c, QSIM_E_INVAL, "program does not belong to this context");
+    for (const DevChunk &dc : p->chunks) {
+        s = launch_chunk(c, dc);
+        if (s != QSIM_OK) return s;
+    }
+    return QSIM_OK;
+}
+
+qsim_status qsim_program_get_info(const qsim_program *p, qsim_program_info *info) {
+    if (!p || !info) return QSIM_E_INVAL;
+    *info = p->info;
+    return QSIM_OK;
+}
+
+qsim_status qsim_program_free(qsim_program *p) {
+    if (!p) return QSIM_OK;
+    if (p->owner) {
+        cudaSetDevice(p->owner->device);
+        for (auto &dc : p->chunks) release_chunk(p->owner, dc);
+    }
+    delete p;
+    return QSIM_OK;
+}
+
+qsim_status qsim_measure(qsim_ctx *c, int qubit, uint64_t seed, int mode, int *outcome, double *prob) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (qubit < 0 || qubit >= c->n) return fail(c, QSIM_E_INVAL, "qubit out of range");
+    if (mode != 0 && mode != 1) return fail(c, QSIM_E_INVAL, "mode must be 0 or 1");
+    const uint64_t idx = c->log_n;
+    s = launch_measure(c, qubit, mode, 0, seed);
+    if (s != QSIM_OK) return s;
+    if (!outcome && !prob) return QSIM_OK;
+    MeasRec rec;
+    CK(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(MeasCtl), cudaMemcpyDeviceToHost, c->stream), "readback");
+    CK(cudaMemcpyAsync(&rec, c->log + idx, sizeof(rec), cudaMemcpyDeviceToHost, c->stream), "readback");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (c->h_ctl->status == QSIM_E_ZEROPROB) {
+        if (c->h_ctl->fail_log == idx) {
+            if (outcome) *outcome = -1;
+            if (prob) *prob = rec.prob;
+            return fail(c, QSIM_E_ZEROPROB, "assertion failed: P(0) <= threshold");
+        }
+        return fail(c, QSIM_E_ZEROPROB, "an earlier assertion-mode measurement failed");
+    }
+    if (outcome) *outcome = rec.outcome;
+    if (prob) *prob = rec.prob;
+    return QSIM_OK;
+}
+
+qsim_status qsim_prob(qsim_ctx *c, int qubit, double *p0, double *p1) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (qubit < 0 || qubit >= c->n) return fail(c, QSIM_E_INVAL, "qubit out of range");
+    s = ensure_partials(c, 2 * (size_t)qsim::prob_blocks(c->n));
+    if (s != QSIM_OK) return s;
+    CK(qsim::launch_prob_only(c->dtype, c->state, c->n, qubit, c->partials, c->ctl, c->stream), "prob launch");
+    s = sync_read(c);
+    if (s != QSIM_OK) return s;
+    if (p0) *p0 = c->h_ctl->p0;
+    if (p1) *p1 = c->h_ctl->p1;
+    return QSIM_OK;
+}
+
+qsim_status qsim_outcomes(qsim_ctx *c, int32_t *outcomes, double *probs, size_t cap, size_t *n_total) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    const size_t avail = std::min<uint64_t>(c->log_n, c->log_cap);
+    if (n_total) *n_total = avail;
+    const size_t k = std::min(avail, cap);
+    if (k) {
+        std::vector<MeasRec> recs(k);
+        CK(cudaMemcpy(recs.data(), c->log, k * sizeof(MeasRec), cudaMemcpyDeviceToHost), "log readback");
+        for (size_t i = 0; i < k; i++) {
+            if (outcomes) outcomes[i] = recs[i].outcome;
+            if (probs) probs[i] = recs[i].prob;
+        }
+    }
+    return sync_read(c) == QSIM_E_CUDA ? QSIM_E_CUDA : QSIM_OK;
+}
+
+qsim_status qsim_success_prob(qsim_ctx *c, double *p) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (!p) return fail(c, QSIM_E_INVAL, "p is NULL");
+    s = sync_read(c);
+    *p = c->h_ctl->success;
+    return s;
+}
+
+qsim_status qsim_expect(qsim_ctx *c, const qsim_pauli_term *t, size_t nt, double *out) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (nt == 0) return QSIM_OK;
+    if (!t || !out) return fail(c, QSIM_E_INVAL, "null terms or out");
+    const uint64_t full = c->n >= 64 ? ~0ull : ((1ull << c->n) - 1ull);
+    for (size_t i = 0; i < nt; i++)
+        if ((t[i].x_mask | t[i].z_mask) & ~full) return fail(c, QSIM_E_INVAL, "Pauli term beyond n qubits");
+    const int P = qsim::expect_blocks(c->n);
+    s = ensure_partials(c, (size_t)P * nt);
+    if (s != QSIM_OK) return s;
+    const size_t tb = nt * 3 * sizeof(uint64_t);
+    uint64_t *d_terms = (uint64_t *)dalloc(c, tb);
+    double *d_out = (double *)dalloc(c, nt * sizeof(double));
+    if (!d_terms || !d_out) {
+        dfree(c, d_terms, tb);
+        dfree(c, d_out, nt * sizeof(double));
+        return fail(c, QSIM_E_OOM, "expectation buffers");
+    }
+    static_assert(sizeof(qsim_pauli_term) == 24, "term layout");
+    s = upload(c, d_terms, t, tb);
+    if (s == QSIM_OK) {
+        cudaError_t e = qsim::launch_expect(c->dtype, c->state, c->n, d_terms, nt, c->partials, d_out, c->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "expect launch");
+    }
+    if (s == QSIM_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, d_out, nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "expect readback");
+    }
+    dfree(c, d_terms, tb);
+    dfree(c, d_out, nt * sizeof(double));
+    if (s != QSIM_OK) return s;
+    return sync_read(c);
+}
+
+qsim_status qsim_state(qsim_ctx *c, void *dst, size_t bytes, int dst_is_device) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (!dst || bytes != c->state_bytes) return fail(c, QSIM_E_INVAL, "dst NULL or size mismatch");
+    CK(cudaMemcpyAsync(dst, c->state, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream),
+       "state copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_state(qsim_ctx *c, const void *src, size_t bytes, int src_is_device) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (!src || bytes != c->state_bytes) return fail(c, QSIM_E_INVAL, "src NULL or size mismatch");
+    CK(cudaMemcpyAsync(c->state, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream),
+       "state copy");
+    CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(int32_t), c->stream), "status clear");
+    if (!src_is_device) CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return QSIM_OK;
+}
+
+qsim_status qsim_reset_state(qsim_ctx *c) {
+    if (!c) return fail(nullptr, QSIM_E_INVAL, "null context");
+    if (c->broken) return fail(c, QSIM_E_STATE, "context unusable after an earlier CUDA error");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(qsim::launch_set_basis(c->dtype, c->state, c->n, 0, c->stream), "state reset");
+    MeasCtl init;
+    std::memset(&init, 0, sizeof(init));
+    init.success = 1.0;
+    *c->h_ctl = init;
+    CK(cudaMemcpyAsync(c->ctl, c->h_ctl, sizeof(MeasCtl), cudaMemcpyHostToDevice, c->stream), "control reset");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    c->ordinal = 0;
+    c->log_n = 0;
+    return QSIM_OK;
+}
+
+qsim_status qsim_state_ptr(qsim_ctx *c, void **dptr, size_t *bytes) {
+    if (!c || !dptr) return fail(c, QSIM_E_INVAL, "null argument");
+    *dptr = c->state;
+    if (bytes) *bytes = c->state_bytes;
+    return QSIM_OK;
+}
+
+qsim_status qsim_sync(qsim_ctx *c) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    return sync_read(c);
+}
+
+// ----------------------------------------------------- host-only inspection --
+qsim_status qsim_fuse(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, const double *mats,
+                      size_t nm, const qsim_config *cfg, uint8_t *out_k, uint32_t *out_q,
+                      uint64_t *out_mat, size_t cap_ops, double *out_mats, size_t cap_mat_doubles,
+                      size_t *n_ops, size_t *n_mat_doubles) {
+    if (n < 1 || n > 34 || (ng && !g)) return fail(nullptr, QSIM_E_INVAL, "bad arguments");
+    std::string err;
+    if (!qsim::validate(n, g, ng, mats, nm, err)) return fail(nullptr, QSIM_E_INVAL, err);
+    HostProgram hp;
+    qsim::compile(n, dtype, qsim::config_from(cfg), g, ng, mats, nm, hp);
+    if (n_ops) *n_ops = hp.ops.size();
+    if (n_mat_doubles) *n_mat_doubles = hp.pool.size() * 2;
+    if (hp.ops.size() > cap_ops || hp.pool.size() * 2 > cap_mat_doubles)
+        return fail(nullptr, QSIM_E_INVAL, "output capacity too small");
+    for (size_t i = 0; i < hp.ops.size(); i++) {
+        const qsim::FOp &o = hp.ops[i];
+        out_k[i] = o.k;
+        for (int j = 0; j < 6; j++) out_q[6 * i + j] = 0;
+        if (o.k) {
+            for (int j = 0; j < o.k; j++) out_q[6 * i + j] = o.q[j];
+            out_mat[i] = o.mat * 2;
+        } else {
+            out_q[6 * i] = o.q[0];
+            out_q[6 * i + 1] = o.ev == qsim::EV_MEASURE ? QSIM_OP_MEASURE
+                               : o.ev == qsim::EV_RESET  ? QSIM_OP_RESET
+                                                         : QSIM_OP_BARRIER;
+            out_q[6 * i + 2] = o.flags;
+            out_mat[i] = 0;
+        }
+    }
+    if (!hp.pool.empty()) std::memcpy(out_mats, hp.pool.data(), hp.pool.size() * 16);
+    return QSIM_OK;
+}
+
+qsim_status qsim_schedule(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, const double *mats,
+                          size_t nm, const qsim_config *cfg, uint64_t *out_tile, uint64_t *out_first,
+                          uint32_t *out_count, size_t cap, size_t *n_passes) {
+    if (n < 1 || n > 34 || (ng && !g)) return fail(nullptr, QSIM_E_INVAL, "bad arguments");
+    std::string err;
+    if (!qsim::validate(n, g, ng, mats, nm, err)) return fail(nullptr, QSIM_E_INVAL, err);
+    HostProgram hp;
+    qsim::compile(n, dtype, qsim::config_from(cfg), g, ng, mats, nm, hp);
+    if (n_passes) *n_passes = hp.passes.size();
+    if (hp.passes.size() > cap) return fail(nullptr, QSIM_E_INVAL, "output capacity too small");
+    for (size_t i = 0; i < hp.passes.size(); i++) {
+        out_tile[i] = hp.passes[i].ev ? 0 : hp.passes[i].tile;
+        out_first[i] = hp.passes[i].first;
+        out_count[i] = hp.passes[i].count;
+    }
+    return QSIM_OK;
+}
+
+}  // extern "C"

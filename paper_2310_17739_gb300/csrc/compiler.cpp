@@ -1,0 +1,588 @@
+// compiler.cpp -- host compiler: gate matrices, fusion (paper, Section "Gate
+// Fusion"), pass scheduling into shared-memory tiles, k-qubit block merging.
+//
+// Fusion follows the paper's four stages, realised in one streaming pass over
+// the gate records (every merge is exact algebra, so the grouping only changes
+// rounding):
+//   stage 1  consecutive 1-qubit gates on one qubit are multiplied into one
+//            pending 2x2 (C1);
+//   stage 2  a 2-qubit gate absorbs the pending C1 of both its qubits
+//            (backward absorption); a C1 left pending at a measurement, reset
+//            or barrier (on any qubit), or at the end of the stream, is
+//            absorbed forward into the last 2-qubit op on that qubit if no
+//            other op touched the qubit since, else emitted as a C1;
+//   stage 3  every 2-qubit matrix is expressed with its lower qubit as local
+//            bit 0 (U(b,a) -> SWAP U(a,b) SWAP, done as a basis permutation of
+//            the 4x4 rather than two extra SWAP gates);
+//   stage 4  a 2-qubit gate whose two qubits were last touched by the same C2
+//            (same pair, nothing in between on either wire) is multiplied into
+//            it -- this also merges CX gates with control and target swapped.
+#include "compiler.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace qsim {
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+inline cd expi(double a) { return cd(std::cos(a), std::sin(a)); }
+
+bool is_1q(int op) { return op >= QSIM_OP_ID && op <= QSIM_OP_C1; }
+bool is_2q(int op) { return op >= QSIM_OP_CX && op <= QSIM_OP_C2; }
+bool is_event(int op) {
+    return op == QSIM_OP_MEASURE || op == QSIM_OP_RESET || op == QSIM_OP_BARRIER;
+}
+
+// 2x2 of the named one-qubit gates, row-major.
+bool named_1q(int op, const double *p, cd *u) {
+    const cd I(0, 1);
+    const double r = std::sqrt(0.5);
+    auto set = [&](cd a, cd b, cd c, cd d) { u[0] = a; u[1] = b; u[2] = c; u[3] = d; };
+    switch (op) {
+        case QSIM_OP_ID: set(1, 0, 0, 1); return true;
+        case QSIM_OP_X: set(0, 1, 1, 0); return true;
+        case QSIM_OP_Y: set(0, -I, I, 0); return true;
+        case QSIM_OP_Z: set(1, 0, 0, -1); return true;
+        case QSIM_OP_H: set(r, r, r, -r); return true;
+        case QSIM_OP_S: set(1, 0, 0, I); return true;
+        case QSIM_OP_SDG: set(1, 0, 0, -I); return true;
+        case QSIM_OP_T: set(1, 0, 0, expi(kPi / 4)); return true;
+        case QSIM_OP_TDG: set(1, 0, 0, expi(-kPi / 4)); return true;
+        case QSIM_OP_RX: {
+            double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+            set(c, cd(0, -s), cd(0, -s), c);
+            return true;
+        }
+        case QSIM_OP_RY: {
+            double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+            set(c, -s, s, c);
+            return true;
+        }
+        case QSIM_OP_RZ: set(expi(-p[0] / 2), 0, 0, expi(p[0] / 2)); return true;
+        case QSIM_OP_U1: set(1, 0, 0, expi(p[0])); return true;
+        case QSIM_OP_U2:
+        case QSIM_OP_U3: {
+            double t = op == QSIM_OP_U2 ? kPi / 2 : p[0];
+            double ph = op == QSIM_OP_U2 ? p[0] : p[1];
+            double la = op == QSIM_OP_U2 ? p[1] : p[2];
+            double c = std::cos(t / 2), s = std::sin(t / 2);
+            set(c, -expi(la) * s, expi(ph) * s, expi(ph + la) * c);
+            return true;
+        }
+        default: return false;
+    }
+}
+
+// 4x4 of the named two-qubit gates in basis l = b_q0 + 2 b_q1.
+bool named_2q(int op, const double *p, cd *m) {
+    for (int i = 0; i < 16; i++) m[i] = 0;
+    int target_op = -1;
+    switch (op) {
+        case QSIM_OP_CX: target_op = QSIM_OP_X; break;
+        case QSIM_OP_CY: target_op = QSIM_OP_Y; break;
+        case QSIM_OP_CZ: target_op = QSIM_OP_Z; break;
+        case QSIM_OP_CH: target_op = QSIM_OP_H; break;
+        case QSIM_OP_CRX: target_op = QSIM_OP_RX; break;
+        case QSIM_OP_CRY: target_op = QSIM_OP_RY; break;
+        case QSIM_OP_CRZ: target_op = QSIM_OP_RZ; break;
+        case QSIM_OP_CU1: target_op = QSIM_OP_U1; break;
+        case QSIM_OP_CU3: target_op = QSIM_OP_U3; break;
+        default: break;
+    }
+    if (target_op >= 0) {
+        cd u[4];
+        named_1q(target_op, p, u);
+        // control = local bit 0; control 0 -> identity on the target bit.
+        m[0 * 4 + 0] = 1;
+        m[2 * 4 + 2] = 1;
+        m[1 * 4 + 1] = u[0];
+        m[1 * 4 + 3] = u[1];
+        m[3 * 4 + 1] = u[2];
+        m[3 * 4 + 3] = u[3];
+        return true;
+    }
+    switch (op) {
+        case QSIM_OP_SWAP:
+            m[0] = 1; m[1 * 4 + 2] = 1; m[2 * 4 + 1] = 1; m[15] = 1;
+            return true;
+        case QSIM_OP_RXX: {
+            double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+            for (int l = 0; l < 4; l++) {
+                m[l * 4 + l] = c;
+                m[l * 4 + (3 - l)] = cd(0, -s);
+            }
+            return true;
+        }
+        case QSIM_OP_RZZ:
+            m[0] = expi(-p[0] / 2);
+            m[5] = expi(p[0] / 2);
+            m[10] = expi(p[0] / 2);
+            m[15] = expi(-p[0] / 2);
+            return true;
+        default: return false;
+    }
+}
+
+// Matrix helpers on row-major 2^k x 2^k arrays.
+// Left-multiply by U (2x2) acting on local bit j: M <- (U on bit j) * M.
+void left_1q(cd *M, int k, int j, const cd *U) {
+    const int D = 1 << k, b = 1 << j;
+    for (int r0 = 0; r0 < D; r0++) {
+        if (r0 & b) continue;
+        const int r1 = r0 | b;
+        for (int c = 0; c < D; c++) {
+            cd x0 = M[r0 * D + c], x1 = M[r1 * D + c];
+            M[r0 * D + c] = U[0] * x0 + U[1] * x1;
+            M[r1 * D + c] = U[2] * x0 + U[3] * x1;
+        }
+    }
+}
+// Right-multiply by U acting on local bit j: M <- M * (U on bit j).
+void right_1q(cd *M, int k, int j, const cd *U) {
+    const int D = 1 << k, b = 1 << j;
+    for (int r = 0; r < D; r++) {
+        for (int c0 = 0; c0 < D; c0++) {
+            if (c0 & b) continue;
+            const int c1 = c0 | b;
+            cd y0 = M[r * D + c0], y1 = M[r * D + c1];
+            M[r * D + c0] = y0 * U[0] + y1 * U[2];
+            M[r * D + c1] = y0 * U[1] + y1 * U[3];
+        }
+    }
+}
+void matmul(const cd *A, const cd *B, cd *C, int D) {  // C = A * B
+    for (int r = 0; r < D; r++)
+        for (int c = 0; c < D; c++) {
+            cd s = 0;
+            for (int t = 0; t < D; t++) s += A[r * D + t] * B[t * D + c];
+            C[r * D + c] = s;
+        }
+}
+// Swap local bits 0 and 1 of a 4x4 (basis permutation P M P).
+void swap_bits_4(cd *M) {
+    static const int perm[4] = {0, 2, 1, 3};
+    cd T[16];
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) T[perm[r] * 4 + perm[c]] = M[r * 4 + c];
+    std::memcpy(static_cast<void *>(M), T, sizeof(T));
+}
+
+// Expand a k-qubit matrix (qubits qs) into the u-qubit space us (qs subset of us).
+void expand(const cd *M, int k, const uint32_t *qs, int u, const uint32_t *us, cd *E) {
+    int pos[kMaxK];
+    for (int j = 0; j < k; j++)
+        for (int t = 0; t < u; t++)
+            if (us[t] == qs[j]) pos[j] = t;
+    uint32_t inmask = 0;
+    for (int j = 0; j < k; j++) inmask |= 1u << pos[j];
+    const int D = 1 << u, d = 1 << k;
+    for (int r = 0; r < D; r++) {
+        int lr = 0;
+        for (int j = 0; j < k; j++) lr |= ((r >> pos[j]) & 1) << j;
+        for (int c = 0; c < D; c++) {
+            if ((r & ~inmask) != (c & ~inmask)) {
+                E[r * D + c] = 0;
+                continue;
+            }
+            int lc = 0;
+            for (int j = 0; j < k; j++) lc |= ((c >> pos[j]) & 1) << j;
+            E[r * D + c] = M[lr * d + lc];
+        }
+    }
+}
+// E (u-qubit, 2^u x 2^u) <- B(op on qubits qb) * E
+void left_apply(cd *E, int u, const uint32_t *us, const cd *B, int kb, const uint32_t *qb) {
+    int pos[kMaxK];
+    for (int j = 0; j < kb; j++)
+        for (int t = 0; t < u; t++)
+            if (us[t] == qb[j]) pos[j] = t;
+    uint32_t bmask = 0;
+    for (int j = 0; j < kb; j++) bmask |= 1u << pos[j];
+    const int D = 1 << u, d = 1 << kb;
+    cd x[1 << kMaxK], y[1 << kMaxK];
+    int off[1 << kMaxK];
+    for (int l = 0; l < d; l++) {
+        int o = 0;
+        for (int j = 0; j < kb; j++) o |= ((l >> j) & 1) << pos[j];
+        off[l] = o;
+    }
+    for (int c = 0; c < D; c++) {
+        for (int r0 = 0; r0 < D; r0++) {
+            if (r0 & bmask) continue;
+            for (int l = 0; l < d; l++) x[l] = E[(r0 | off[l]) * D + c];
+            for (int a = 0; a < d; a++) {
+                cd s = 0;
+                for (int b = 0; b < d; b++) s += B[a * d + b] * x[b];
+                y[a] = s;
+            }
+            for (int l = 0; l < d; l++) E[(r0 | off[l]) * D + c] = y[l];
+        }
+    }
+}
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ config --
+Config config_from(const qsim_config *c) {
+    Config k;
+    if (!c) return k;
+    k.fusion = c->fusion;
+    k.k_max = c->k_max;
+    k.tile_bits = c->tile_bits;
+    k.threads = c->threads;
+    k.chunk_gates = c->chunk_gates;
+    k.lookahead = c->lookahead;
+    k.compile_threads = c->compile_threads;
+    return k;
+}
+
+void config_to(const Config &c, qsim_config *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->fusion = c.fusion;
+    o->k_max = c.k_max;
+    o->tile_bits = c.tile_bits;
+    o->threads = c.threads;
+    o->chunk_gates = c.chunk_gates;
+    o->lookahead = c.lookahead;
+    o->compile_threads = c.compile_threads;
+}
+
+static int max_tile_bits(qsim_dtype dt) { return dt == QSIM_C64 ? 14 : 13; }
+
+int tile_bits_for(const Config &cfg, int n, qsim_dtype dtype) {
+    const int mx = max_tile_bits(dtype);
+    int m = cfg.tile_bits;
+    if (m <= 0) {
+        // Resident (whole state in one block) for small states, otherwise the
+        // largest tile that still leaves >= 256 tiles to spread over 152 SMs.
+        if (n <= 10) return n;
+        m = std::max(10, std::min(mx, n - 8));
+    }
+    m = std::min(m, mx);
+    m = std::min(m, n);
+    return std::max(m, 1);
+}
+
+int forced_low_bits(qsim_dtype dtype, int m) {
+    int L = dtype == QSIM_C64 ? 4 : 3;  // 16 x 8 B or 8 x 16 B = 128-byte runs
+    return std::min(L, m);
+}
+
+// ------------------------------------------------------------------ matrices --
+int gate_matrix(const qsim_gate &g, const double *mats, size_t n_mats, cd *out) {
+    if (g.op == QSIM_OP_C1 || g.op == QSIM_OP_C2) {
+        const int d = g.op == QSIM_OP_C1 ? 2 : 4;
+        if (!mats || (size_t)g.mat + 2 * d * d > n_mats) return -1;
+        for (int i = 0; i < d * d; i++) out[i] = cd(mats[g.mat + 2 * i], mats[g.mat + 2 * i + 1]);
+        return d;
+    }
+    if (is_1q(g.op)) return named_1q(g.op, g.p, out) ? 2 : -1;
+    if (is_2q(g.op)) return named_2q(g.op, g.p, out) ? 4 : -1;
+    if (is_event(g.op)) return 0;
+    return -1;
+}
+
+bool validate(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
+              std::string &err) {
+    for (size_t i = 0; i < n_gates; i++) {
+        const qsim_gate &x = g[i];
+        const int op = x.op;
+        bool ok = true;
+        if (is_1q(op) || op == QSIM_OP_MEASURE || op == QSIM_OP_RESET) {
+            ok = x.q0 < (uint32_t)n;
+        } else if (is_2q(op)) {
+            ok = x.q0 < (uint32_t)n && x.q1 < (uint32_t)n && x.q0 != x.q1;
+        } else if (op != QSIM_OP_BARRIER) {
+            ok = false;
+        }
+        if (ok && (op == QSIM_OP_C1 || op == QSIM_OP_C2)) {
+            const size_t need = op == QSIM_OP_C1 ? 8 : 32;
+            ok = mats != nullptr && (size_t)x.mat + need <= n_mats;
+        }
+        if (ok && !is_event(op)) {
+            for (int j = 0; j < 3; j++) ok = ok && std::isfinite(x.p[j]);
+        }
+        if (!ok) {
+            err = "malformed gate record " + std::to_string(i) + " (op " + std::to_string(op) +
+                  ", q0 " + std::to_string(x.q0) + ", q1 " + std::to_string(x.q1) + ")";
+            return false;
+        }
+    }
+    return true;
+}
+
+// -------------------------------------------------------------------- fusion --
+void fuse(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
+          int fusion, std::vector<FOp> &ops, std::vector<cd> &pool, uint64_t *n_meas) {
+    ops.clear();
+    pool.clear();
+    ops.reserve(n_gates / 2 + 16);
+    pool.reserve(n_gates * 8 + 64);
+    uint64_t meas = 0;
+    std::vector<cd> pend(4 * (size_t)n);
+    std::vector<char> has_pend(n, 0);
+    std::vector<int64_t> open2(n, -1);  // last op on the qubit, if a C2 that can still absorb
+    cd m[16], t[16];
+
+    auto emit_mat = [&](int k, const uint32_t *qs, const cd *M) -> int64_t {
+        FOp o;
+        o.k = (uint8_t)k;
+        for (int j = 0; j < k; j++) o.q[j] = qs[j];
+        o.mat = pool.size();
+        pool.insert(pool.end(), M, M + (1 << (2 * k)));
+        ops.push_back(o);
+        return (int64_t)ops.size() - 1;
+    };
+    auto flush = [&](int q) {
+        if (!has_pend[q]) return;
+        cd *U = &pend[4 * (size_t)q];
+        const int64_t idx = open2[q];
+        if (idx >= 0) {  // forward absorption into the last C2 on q
+            FOp &o = ops[idx];
+            const int j = o.q[0] == (uint32_t)q ? 0 : 1;
+            left_1q(&pool[o.mat], 2, j, U);
+        } else {
+            uint32_t qs[1] = {(uint32_t)q};
+            emit_mat(1, qs, U);
+        }
+        has_pend[q] = 0;
+    };
+
+    for (size_t i = 0; i < n_gates; i++) {
+        const qsim_gate &x = g[i];
+        const int op = x.op;
+        if (is_event(op)) {
+            FOp e;
+            e.k = 0;
+            e.ev = op == QSIM_OP_MEASURE ? EV_MEASURE : op == QSIM_OP_RESET ? EV_RESET : EV_BARRIER;
+            e.flags = x.flags;
+            e.q[0] = x.q0;
+            // Every event is a fusion barrier on all qubits: no gate crosses a
+            // measurement, so the state an event sees (and the state left by a
+            // failed assertion) is the state of the unfused stream at that point.
+            if (fusion) {
+                for (int q = 0; q < n; q++) {
+                    flush(q);
+                    open2[q] = -1;
+                }
+            }
+            if (op != QSIM_OP_BARRIER) meas++;
+            ops.push_back(e);
+            continue;
+        }
+        const int d = gate_matrix(x, mats, n_mats, m);
+        if (d == 2) {
+            const int q = (int)x.q0;
+            if (!fusion) {
+                uint32_t qs[1] = {(uint32_t)q};
+                emit_mat(1, qs, m);
+                continue;
+            }
+            cd *U = &pend[4 * (size_t)q];
+            if (has_pend[q]) {  // stage 1: U <- m * U
+                cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
+                           m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
+                for (int j = 0; j < 4; j++) U[j] = r[j];
+            } else {
+                for (int j = 0; j < 4; j++) U[j] = m[j];
+                has_pend[q] = 1;
+            }
+            continue;
+        }
+        // two-qubit gate; stage 3: lower qubit becomes local bit 0
+        uint32_t p = x.q0, q = x.q1;
+        if (p > q) {
+            swap_bits_4(m);
+            std::swap(p, q);
+        }
+        if (!fusion) {
+            uint32_t qs[2] = {p, q};
+            emit_mat(2, qs, m);
+            continue;
+        }
+        // stage 2 (backward): absorb pending C1 on p (bit 0) and q (bit 1)
+        if (has_pend[p]) { right_1q(m, 2, 0, &pend[4 * (size_t)p]); has_pend[p] = 0; }
+        if (has_pend[q]) { right_1q(m, 2, 1, &pend[4 * (size_t)q]); has_pend[q] = 0; }
+        const int64_t a = open2[p], b = open2[q];
+        if (a >= 0 && a == b) {  // stage 4: same pair, nothing in between
+            cd *M = &pool[ops[a].mat];
+            matmul(m, M, t, 4);
+            std::memcpy(static_cast<void *>(M), t, sizeof(t));
+        } else {
+            uint32_t qs[2] = {p, q};
+            const int64_t idx = emit_mat(2, qs, m);
+            open2[p] = open2[q] = idx;
+        }
+    }
+    if (fusion)
+        for (int q = 0; q < n; q++) flush(q);
+    if (n_meas) *n_meas = meas;
+}
+
+// --------------------------------------------------------- k-qubit merging --
+namespace {
+
+double merge_cost(int k, qsim_dtype dt) {
+    // Per-amplitude cost of one op in a shared-memory tile: one read+write
+    // sweep (~16 FMA-equivalents of shared-memory bandwidth for c64) plus
+    // 4 * 2^k FMAs (2^k complex multiply-adds).  FP64 FMAs are far slower than
+    // FP32 ones on this part, so for c128 the arithmetic term dominates.
+    const double alu = 4.0 * (1 << k);
+    return dt == QSIM_C64 ? 16.0 + alu : 16.0 + 16.0 * alu;
+}
+
+void merge_pass(std::vector<FOp> &ops, std::vector<cd> &pool, size_t first, size_t count,
+                int k_max, qsim_dtype dt, std::vector<FOp> &out) {
+    if (count == 0) return;
+    FOp cur = ops[first];
+    std::vector<cd> curM(pool.begin() + cur.mat, pool.begin() + cur.mat + (1 << (2 * cur.k)));
+    std::vector<cd> E;
+    auto flush = [&]() {
+        cur.mat = pool.size();
+        pool.insert(pool.end(), curM.begin(), curM.end());
+        out.push_back(cur);
+    };
+    for (size_t i = first + 1; i < first + count; i++) {
+        const FOp &o = ops[i];
+        const uint64_t um = cur.mask() | o.mask();
+        const int u = popc(um);
+        if (u <= k_max && merge_cost(u, dt) <= merge_cost(cur.k, dt) + merge_cost(o.k, dt)) {
+            uint32_t us[kMaxK];
+            int t = 0;
+            for (int b = 0; b < 64; b++)
+                if ((um >> b) & 1) us[t++] = (uint32_t)b;
+            E.assign((size_t)1 << (2 * u), cd(0));
+            expand(curM.data(), cur.k, cur.q, u, us, E.data());
+            left_apply(E.data(), u, us, &pool[o.mat], o.k, o.q);
+            cur.k = (uint8_t)u;
+            for (int j = 0; j < u; j++) cur.q[j] = us[j];
+            curM.swap(E);
+        } else {
+            flush();
+            cur = o;
+            curM.assign(pool.begin() + o.mat, pool.begin() + o.mat + (1 << (2 * o.k)));
+        }
+    }
+    flush();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- schedule --
+void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, size_t n_gates,
+             const double *mats, size_t n_mats, HostProgram &out) {
+    out = HostProgram();
+    out.n = n;
+    out.gates = n_gates;
+    std::vector<FOp> ops;
+    std::vector<cd> pool;
+    fuse(n, g, n_gates, mats, n_mats, cfg.fusion, ops, pool, &out.measurements);
+
+    const int m = tile_bits_for(cfg, n, dtype);
+    out.m = m;
+    out.resident = (m == n);
+    const int L = forced_low_bits(dtype, m);
+    const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
+    const uint64_t forced = out.resident ? all : ((1ull << L) - 1);
+    const size_t W = cfg.lookahead > 0 ? (size_t)cfg.lookahead : 64;
+    const int k_max = std::max(2, std::min(cfg.k_max > 0 ? cfg.k_max : 2, std::min(5, m)));
+
+    // Doubly linked list over not-yet-scheduled ops (in stream order).
+    const size_t N = ops.size();
+    std::vector<int64_t> nxt(N + 1), prv(N + 1);
+    const int64_t HEAD = (int64_t)N;  // sentinel
+    for (size_t i = 0; i < N; i++) {
+        nxt[i] = (int64_t)i + 1 < (int64_t)N ? (int64_t)i + 1 : HEAD;
+        prv[i] = i == 0 ? HEAD : (int64_t)i - 1;
+    }
+    nxt[HEAD] = N ? 0 : HEAD;
+    prv[HEAD] = N ? (int64_t)N - 1 : HEAD;
+    auto unlink = [&](int64_t i) {
+        nxt[prv[i]] = nxt[i];
+        prv[nxt[i]] = prv[i];
+    };
+
+    std::vector<FOp> sched;
+    sched.reserve(N);
+    std::vector<cd> spool;
+    spool.reserve(pool.size());
+    std::vector<size_t> taken;
+
+    while (nxt[HEAD] != HEAD) {
+        const int64_t f = nxt[HEAD];
+        if (ops[f].k == 0) {  // event: its own pass, never reordered
+            unlink(f);
+            if (ops[f].ev != EV_BARRIER) {
+                Pass p;
+                p.first = sched.size();
+                p.count = 1;
+                p.ev = ops[f].ev;
+                p.flags = ops[f].flags;
+                p.q = ops[f].q[0];
+                sched.push_back(ops[f]);
+                out.passes.push_back(p);
+            }
+            continue;
+        }
+        uint64_t T = forced, blocked = 0;
+        size_t skipped = 0;
+        taken.clear();
+        for (int64_t i = f; i != HEAD && skipped < W;) {
+            const int64_t ni = nxt[i];
+            const FOp &o = ops[i];
+            if (o.k == 0) break;  // events bound the scan
+            const uint64_t Q = o.mask();
+            if (!(Q & blocked) && popc(T | Q) <= m) {
+                T |= Q;
+                taken.push_back((size_t)i);
+                unlink(i);
+            } else {
+                blocked |= Q;
+                skipped++;
+                if (popc(blocked) >= n) break;
+            }
+            i = ni;
+        }
+        // Pad the tile to exactly m qubits (lowest unused first).
+        for (int b = 0; b < n && popc(T) < m; b++) T |= 1ull << b;
+        Pass p;
+        p.tile = T;
+        p.first = sched.size();
+        if (cfg.k_max > 2) {
+            // merge in the pass's order into <= k_max-qubit dense blocks
+            std::vector<FOp> tmp;
+            tmp.reserve(taken.size());
+            for (size_t t : taken) tmp.push_back(ops[t]);
+            std::vector<FOp> merged;
+            merge_pass(tmp, pool, 0, tmp.size(), k_max, dtype, merged);
+            for (auto &o : merged) {
+                FOp c = o;
+                c.mat = spool.size();
+                spool.insert(spool.end(), pool.begin() + o.mat, pool.begin() + o.mat + (1 << (2 * o.k)));
+                sched.push_back(c);
+            }
+        } else {
+            for (size_t t : taken) {
+                FOp c = ops[t];
+                c.mat = spool.size();
+                spool.insert(spool.end(), pool.begin() + ops[t].mat,
+                             pool.begin() + ops[t].mat + (1 << (2 * ops[t].k)));
+                sched.push_back(c);
+            }
+        }
+        p.count = (uint32_t)(sched.size() - p.first);
+        out.passes.push_back(p);
+    }
+    for (const FOp &o : sched)
+        if (o.k) out.hist[o.k]++;
+    out.ops.swap(sched);
+    out.pool.swap(spool);
+}
+
+}  // namespace qsim

@@ -1,0 +1,99 @@
+// compiler.h -- host-side gate-stream compiler: gate matrices, the four fusion
+// stages of the paper's Section "Gate Fusion", k-qubit block merging, and the
+// shared-memory pass schedule consumed by the sm_103a kernels.
+#pragma once
+
+#include <complex>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxK = 6;         // largest dense block (qubits)
+constexpr int kMaxTileBits = 15; // largest shared-memory tile (qubits)
+
+enum : uint8_t { EV_NONE = 0, EV_MEASURE = 1, EV_RESET = 2, EV_BARRIER = 3 };
+
+// One fused operation.  k > 0: dense 2^k x 2^k matrix at pool[mat], bit j of
+// the local matrix index <-> qubit q[j].  k == 0: an event (measure, reset,
+// barrier) on qubit q[0] (barrier: all qubits).
+struct FOp {
+    uint8_t k = 0;
+    uint8_t ev = EV_NONE;
+    uint16_t flags = 0;
+    uint32_t q[kMaxK] = {0, 0, 0, 0, 0, 0};
+    uint64_t mat = 0;
+    uint64_t mask() const {
+        uint64_t m = 0;
+        for (int j = 0; j < k; j++) m |= 1ull << q[j];
+        return m;
+    }
+};
+
+// A pass: full-state sweep over tiles of the qubits in `tile` applying ops
+// [first, first+count) in order; or an event pass (tile == 0, count == 1).
+struct Pass {
+    uint64_t tile = 0;
+    uint64_t first = 0;
+    uint32_t count = 0;
+    uint8_t ev = EV_NONE;
+    uint8_t pad = 0;
+    uint16_t flags = 0;   // event flags (bit 0: assertion mode)
+    uint32_t q = 0;       // event qubit
+};
+
+struct Config {
+    int fusion = 1;
+    int k_max = 2;
+    int tile_bits = 0;
+    int threads = 0;
+    int chunk_gates = 0;
+    int lookahead = 0;
+    int compile_threads = 0;
+};
+
+Config config_from(const qsim_config *c);
+void config_to(const Config &c, qsim_config *out);
+
+// Tile size (qubits) used for an n-qubit state of this dtype.
+int tile_bits_for(const Config &cfg, int n, qsim_dtype dtype);
+// Qubits always kept in every tile so that tile rows are 128-byte runs.
+int forced_low_bits(qsim_dtype dtype, int m);
+
+// Compiled host program: fused ops (with FP64 matrices) in execution order and
+// the pass schedule over them.
+struct HostProgram {
+    int n = 0;
+    int m = 0;                 // tile bits
+    bool resident = false;     // whole state is one tile
+    std::vector<FOp> ops;
+    std::vector<cd> pool;
+    std::vector<Pass> passes;
+    uint64_t gates = 0;
+    uint64_t measurements = 0;
+    uint64_t hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// Matrix of one gate record (dim 2 or 4, row-major, 2q basis l = b_q0 + 2 b_q1).
+// Returns the dimension, or 0 for a non-unitary record, -1 for an unknown op.
+int gate_matrix(const qsim_gate &g, const double *mats, size_t n_mats, cd *out);
+
+// Validates records; on error returns false and fills err.
+bool validate(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
+              std::string &err);
+
+// Stages 1-4 of the paper (fusion=1) or one op per gate (fusion=0).
+void fuse(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
+          int fusion, std::vector<FOp> &ops, std::vector<cd> &pool, uint64_t *n_meas);
+
+// Full compile of one stream (fusion + schedule + k-merge) for n qubits.
+void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, size_t n_gates,
+             const double *mats, size_t n_mats, HostProgram &out);
+
+}  // namespace qsim

@@ -1,0 +1,693 @@
+// kernels.cu -- sm_103a kernels of the state-vector hot path.
+//
+//   k_tile_pass     one pass of the fused program: each block gathers the
+//                   2^m amplitudes of one tile (the non-tile qubits fixed by
+//                   blockIdx) into shared memory, applies every op of the pass
+//                   (Eq. (1q-op)/(2q-op) generalised to dense 2^k blocks on
+//                   tile-local qubits), and writes the tile back.
+//   k_resident      the whole state lives in one block's shared memory and the
+//                   whole instruction stream -- dense ops, measurements, resets
+//                   -- runs in one launch (one block per state for batches).
+//   k_prob          FP64 Born probabilities of one qubit: per-block partials,
+//                   then the last block to arrive sums them in block order,
+//                   draws (or asserts) the outcome and writes the scale.
+//   k_collapse      zero the rejected half, scale the kept half by
+//                   1/sqrt(p_outcome) in FP64 (RESET: move |1> onto |0>).
+//   k_expect        <psi|P_t|psi> partial sums in FP64 per (block, term),
+//                   k_expect_final sums them in block order.
+//
+// State layout: 2^n interleaved (re, im) amplitudes, qubit q = index bit q.
+// Every wait in this file is a __syncthreads; no kernel spins on memory.
+#include "kernels.h"
+
+#include <cstdint>
+
+namespace qsim {
+
+namespace {
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+__device__ __forceinline__ float2 czero(float2) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 czero(double2) { return make_double2(0.0, 0.0); }
+
+__device__ __forceinline__ void cmac(float2 &acc, const float2 m, const float2 x) {
+    acc.x = fmaf(m.x, x.x, acc.x);
+    acc.x = fmaf(-m.y, x.y, acc.x);
+    acc.y = fmaf(m.x, x.y, acc.y);
+    acc.y = fmaf(m.y, x.x, acc.y);
+}
+__device__ __forceinline__ void cmac(double2 &acc, const double2 m, const double2 x) {
+    acc.x = fma(m.x, x.x, acc.x);
+    acc.x = fma(-m.y, x.y, acc.x);
+    acc.y = fma(m.x, x.y, acc.y);
+    acc.y = fma(m.y, x.x, acc.y);
+}
+__device__ __forceinline__ double norm2(float2 a) {
+    double x = a.x, y = a.y;
+    return x * x + y * y;
+}
+__device__ __forceinline__ double norm2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float2 scale_by(float2 a, double s) {
+    return make_float2((float)((double)a.x * s), (float)((double)a.y * s));
+}
+__device__ __forceinline__ double2 scale_by(double2 a, double s) {
+    return make_double2(a.x * s, a.y * s);
+}
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d(double2 a) { return a; }
+
+__device__ __forceinline__ unsigned ins0(unsigned x, int p) {
+    return ((x >> p) << (p + 1)) | (x & ((1u << p) - 1u));
+}
+__device__ __forceinline__ uint64_t ins0_64(uint64_t x, int p) {
+    return ((x >> p) << (p + 1)) | (x & ((1ull << p) - 1ull));
+}
+
+// ------------------------------------------------------ Philox4x64-10 --
+// Salmon et al., SC'11: 10 rounds of the 4x64 bijection with key schedule
+// k += (W0, W1) between rounds.
+__device__ __forceinline__ uint64_t philox_word0(uint64_t ctr0, uint64_t seed) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr0, c1 = 0, c2 = 0, c3 = 0, k0 = seed, k1 = 0;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return c0;
+}
+__device__ __forceinline__ double draw_u01(uint64_t seed, uint64_t k) {
+    return (double)(philox_word0(k, seed) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+struct Decision {
+    int outcome;
+    int fail;
+    double scale;
+    double prob;
+};
+
+// Outcome rule of the measurement (draw or assertion) from the raw sums.
+__device__ Decision decide(double s0, double s1, int mode, int reset, uint64_t seed,
+                           uint64_t ordinal, double thr) {
+    Decision d;
+    const double tot = s0 + s1;
+    const double P0 = s0 / tot;
+    d.fail = 0;
+    if ((mode & 1) && !reset) {
+        if (!(P0 > thr)) {
+            d.fail = 1;
+            d.outcome = -1;
+            d.prob = P0;
+            d.scale = 1.0;
+            return d;
+        }
+        d.outcome = 0;
+    } else {
+        const double u = draw_u01(seed, ordinal);
+        d.outcome = (u < P0) ? 0 : 1;
+    }
+    const double p_out = d.outcome ? s1 : s0;
+    d.scale = 1.0 / sqrt(p_out);
+    d.prob = d.outcome ? s1 / tot : P0;
+    return d;
+}
+
+// Fixed-shape block reduction of two doubles (deterministic order).
+template <int NT>
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *red /* 2*NT/32 */) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[2 * w] = a;
+        red[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int i = 0; i < NT / 32; i++) {
+            x += red[2 * i];
+            y += red[2 * i + 1];
+        }
+        red[0] = x;
+        red[1] = y;
+    }
+    __syncthreads();
+    a = red[0];
+    b = red[1];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ dense ops --
+// Amplitude offsets of the 2^K members of a group (bit j of the local matrix
+// index <-> tile position lq[j]) and the positions sorted for zero insertion.
+template <int K>
+__device__ __forceinline__ void group_layout(const DevOp &op, int *sp, unsigned *off) {
+#pragma unroll
+    for (int j = 0; j < K; j++) sp[j] = op.lq[j];
+#pragma unroll
+    for (int i = 1; i < K; i++)
+#pragma unroll
+        for (int j = i; j > 0; j--)
+            if (sp[j - 1] > sp[j]) {
+                int t = sp[j - 1];
+                sp[j - 1] = sp[j];
+                sp[j] = t;
+            }
+#pragma unroll
+    for (int l = 0; l < (1 << K); l++) {
+        unsigned o = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) o |= ((unsigned)(l >> j) & 1u) << op.lq[j];
+        off[l] = o;
+    }
+}
+
+// K <= 2 (the paper's C1 / C2): the matrix lives in registers.
+template <int K, typename T, int NT>
+__device__ __forceinline__ void apply_dense_reg(T *tile, int m, const DevOp &op, const T *mats) {
+    constexpr int D = 1 << K;
+    int sp[K];
+    unsigned off[D];
+    group_layout<K>(op, sp, off);
+    const T *M = mats + op.mat;
+    T mr[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; i++) mr[i] = M[i];
+    const unsigned G = 1u << (m - K);
+    for (unsigned g = threadIdx.x; g < G; g += NT) {
+        unsigned b = g;
+#pragma unroll
+        for (int j = 0; j < K; j++) b = ins0(b, sp[j]);
+        T x[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) x[l] = tile[b + off[l]];
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            T acc = czero(x[0]);
+#pragma unroll
+            for (int c = 0; c < D; c++) cmac(acc, mr[r * D + c], x[c]);
+            tile[b + off[r]] = acc;
+        }
+    }
+}
+
+// K >= 3: the matrix is staged in shared memory (mbuf, broadcast reads), so
+// that its 4^K entries are not all held in registers.
+template <int K, typename T, int NT>
+__device__ __forceinline__ void apply_dense_smem(T *tile, int m, const DevOp &op, const T *mats,
+                                                 T *mbuf) {
+    constexpr int D = 1 << K;
+    const T *M = mats + op.mat;
+    for (int i = threadIdx.x; i < D * D; i += NT) mbuf[i] = M[i];
+    __syncthreads();
+    int sp[K];
+    unsigned off[D];
+    group_layout<K>(op, sp, off);
+    const unsigned G = 1u << (m - K);
+    for (unsigned g = threadIdx.x; g < G; g += NT) {
+        unsigned b = g;
+#pragma unroll
+        for (int j = 0; j < K; j++) b = ins0(b, sp[j]);
+        T x[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) x[l] = tile[b + off[l]];
+        // every input is in registers before the first output is stored
+#pragma unroll 1
+        for (int r = 0; r < D; r++) {
+            T acc = czero(x[0]);
+            const T *row = mbuf + r * D;
+#pragma unroll
+            for (int c = 0; c < D; c++) cmac(acc, row[c], x[c]);
+            unsigned o = 0;
+#pragma unroll
+            for (int j = 0; j < K; j++) o |= ((unsigned)(r >> j) & 1u) << op.lq[j];
+            tile[b + o] = acc;
+        }
+    }
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const T *mats, T *mbuf) {
+    switch (op.k) {
+        case 1: apply_dense_reg<1, T, NT>(tile, m, op, mats); break;
+        case 2: apply_dense_reg<2, T, NT>(tile, m, op, mats); break;
+        case 3: apply_dense_smem<3, T, NT>(tile, m, op, mats, mbuf); break;
+        case 4: apply_dense_smem<4, T, NT>(tile, m, op, mats, mbuf); break;
+        case 5: apply_dense_smem<5, T, NT>(tile, m, op, mats, mbuf); break;
+        default: break;
+    }
+}
+
+__device__ __forceinline__ DevOp load_op(const DevOp *p) {
+    uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+    DevOp o;
+    *reinterpret_cast<uint4 *>(&o) = v;
+    return o;
+}
+
+// ------------------------------------------------------------ tile pass --
+struct TileArgs {
+    void *state;
+    const DevOp *ops;
+    const void *mats;
+    const MeasCtl *ctl;
+    uint64_t tile_mask;
+    uint32_t n_ops;
+    int n;
+    int m;
+    int L;
+};
+
+constexpr int kMaxHi = 1024;  // 2^(m - L) entries, m - L <= 10
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_tile_pass(TileArgs a) {
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    T *mbuf = tile + (1u << a.m);  // staging of one k >= 3 matrix (<= 32 x 32)
+    __shared__ uint64_t hi_off[kMaxHi];
+    __shared__ int tq[64];
+    __shared__ int ntq[64];
+    if (a.ctl->status) return;
+    if (threadIdx.x == 0) {
+        int t = 0, u = 0;
+        for (int b = 0; b < a.n; b++) {
+            if ((a.tile_mask >> b) & 1ull) tq[t++] = b;
+            else ntq[u++] = b;
+        }
+    }
+    __syncthreads();
+    uint64_t base = 0;
+    {
+        const uint64_t bid = blockIdx.x;
+        for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << ntq[j];
+    }
+    const int L = a.L, hib = a.m - L;
+    for (int r = threadIdx.x; r < (1 << hib); r += NT) {
+        uint64_t o = base;
+        for (int j = 0; j < hib; j++) o |= ((uint64_t)((r >> j) & 1)) << tq[L + j];
+        hi_off[r] = o;
+    }
+    __syncthreads();
+    T *st = reinterpret_cast<T *>(a.state);
+    const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
+    for (unsigned l = threadIdx.x; l < Nt; l += NT) tile[l] = st[hi_off[l >> L] | (l & Lmask)];
+    __syncthreads();
+    const T *mats = reinterpret_cast<const T *>(a.mats);
+    for (uint32_t i = 0; i < a.n_ops; i++) {
+        const DevOp op = load_op(a.ops + i);
+        apply_op<T, NT>(tile, a.m, op, mats, mbuf);
+        __syncthreads();
+    }
+    for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];
+}
+
+// -------------------------------------------------------------- resident --
+template <typename T, int NT>
+__device__ void run_resident(const Instance &in, T *tile, double *red, int *bcast, double *bscale,
+                             int max_n) {
+    const int n = in.n;
+    const unsigned N = 1u << n;
+    T *mbuf = tile + (1u << max_n);
+    T *st = reinterpret_cast<T *>(in.state);
+    if (in.ctl->status) return;
+    for (unsigned l = threadIdx.x; l < N; l += NT) tile[l] = st[l];
+    __syncthreads();
+    const T *mats = reinterpret_cast<const T *>(in.mats);
+    uint64_t ev = 0;
+    bool failed = false;
+    for (uint64_t i = 0; i < in.n_ops; i++) {
+        const DevOp op = load_op(in.ops + i);
+        if (op.k) {
+            apply_op<T, NT>(tile, n, op, mats, mbuf);
+            __syncthreads();
+            continue;
+        }
+        // measurement / reset on qubit q
+        const int q = op.lq[0];
+        double s0 = 0, s1 = 0;
+        for (unsigned l = threadIdx.x; l < N; l += NT) {
+            const double w = norm2(tile[l]);
+            if ((l >> q) & 1u) s1 += w;
+            else s0 += w;
+        }
+        block_sum2<NT>(s0, s1, red);
+        const int reset = op.ev == 2;
+        if (threadIdx.x == 0) {
+            Decision d = decide(s0, s1, op.flags, reset, in.seed, in.ordinal0 + ev, in.thr);
+            const uint64_t li = in.log0 + ev;
+            if (li < in.log_cap) {
+                in.log[li].outcome = d.outcome;
+                in.log[li].prob = d.prob;
+            }
+            if (d.fail) {
+                in.ctl->status = 4;  // QSIM_E_ZEROPROB
+                in.ctl->fail_log = li;
+            } else if ((op.flags & 1) && !reset) {
+                in.ctl->success *= d.prob;
+            }
+            in.ctl->p0 = s0;
+            in.ctl->p1 = s1;
+            bcast[0] = d.fail ? -1 : d.outcome;
+            bscale[0] = d.scale;
+        }
+        __syncthreads();
+        const int outc = bcast[0];
+        const double sc = bscale[0];
+        __syncthreads();
+        ev++;
+        if (outc < 0) {
+            failed = true;
+            break;
+        }
+        const unsigned bq = 1u << q;
+        for (unsigned i2 = threadIdx.x; i2 < N / 2; i2 += NT) {
+            const unsigned i0 = ins0(i2, q), i1 = i0 | bq;
+            const T a0 = tile[i0], a1 = tile[i1];
+            if (outc == 0) {
+                tile[i0] = scale_by(a0, sc);
+            } else if (reset) {
+                tile[i0] = scale_by(a1, sc);
+            } else {
+                tile[i0] = czero(a0);
+            }
+            tile[i1] = (outc == 1 && !reset) ? scale_by(a1, sc) : czero(a1);
+        }
+        __syncthreads();
+    }
+    (void)failed;
+    for (unsigned l = threadIdx.x; l < N; l += NT) st[l] = tile[l];
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_resident_one(Instance in) {
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * NT / 32];
+    __shared__ int bcast[1];
+    __shared__ double bscale[1];
+    run_resident<T, NT>(in, reinterpret_cast<T *>(smem_raw), red, bcast, bscale, in.n);
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_resident_batch(const Instance *insts, int max_n) {
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * NT / 32];
+    __shared__ int bcast[1];
+    __shared__ double bscale[1];
+    const Instance in = insts[blockIdx.x];
+    run_resident<T, NT>(in, reinterpret_cast<T *>(smem_raw), red, bcast, bscale, max_n);
+}
+
+// ----------------------------------------------------------- measurement --
+constexpr int kRedThreads = 256;
+
+template <typename R, bool DECIDE>
+__global__ void __launch_bounds__(kRedThreads) k_prob(const void *state, int n, MeasArgs a,
+                                                      double *partials, MeasCtl *ctl, MeasRec *log) {
+    using T = typename V2<R>::T;
+    __shared__ double red[2 * kRedThreads / 32];
+    __shared__ double part[2 * 1024];
+    __shared__ int last;
+    if (ctl->status) return;
+    const T *st = reinterpret_cast<const T *>(state);
+    const uint64_t N = 1ull << n;
+    const uint64_t chunk = N / gridDim.x;
+    const uint64_t start = chunk * blockIdx.x;
+    double s0 = 0, s1 = 0;
+    for (uint64_t l = threadIdx.x; l < chunk; l += kRedThreads) {
+        const uint64_t i = start + l;
+        const double w = norm2(st[i]);
+        if ((i >> a.q) & 1ull) s1 += w;
+        else s0 += w;
+    }
+    block_sum2<kRedThreads>(s0, s1, red);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = s0;
+        partials[2 * blockIdx.x + 1] = s1;
+        __threadfence();
+        const unsigned t = atomicAdd(&ctl->arrive, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kRedThreads) {
+        part[2 * b] = __ldcg(partials + 2 * b);
+        part[2 * b + 1] = __ldcg(partials + 2 * b + 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (unsigned b = 0; b < gridDim.x; b++) {
+            x += part[2 * b];
+            y += part[2 * b + 1];
+        }
+        ctl->arrive = 0;
+        ctl->p0 = x;
+        ctl->p1 = y;
+        if (DECIDE) {
+            Decision d = decide(x, y, a.mode, a.reset, a.seed, a.ordinal, a.thr);
+            if (a.log_idx < a.log_cap) {
+                log[a.log_idx].outcome = d.outcome;
+                log[a.log_idx].prob = d.prob;
+            }
+            if (d.fail) {
+                ctl->status = 4;  // QSIM_E_ZEROPROB
+                ctl->fail_log = a.log_idx;
+            } else if ((a.mode & 1) && !a.reset) {
+                ctl->success *= d.prob;
+            }
+            ctl->outcome = d.outcome;
+            ctl->scale = d.scale;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_collapse(void *state, int n, int q, int reset,
+                                                  const MeasCtl *ctl) {
+    using T = typename V2<R>::T;
+    if (ctl->status) return;
+    const int outc = ctl->outcome;
+    const double sc = ctl->scale;
+    T *st = reinterpret_cast<T *>(state);
+    const uint64_t half = 1ull << (n - 1), bq = 1ull << q;
+    for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < half; i += (uint64_t)gridDim.x * 256ull) {
+        const uint64_t i0 = ins0_64(i, q), i1 = i0 | bq;
+        const T a0 = st[i0], a1 = st[i1];
+        if (outc == 0) st[i0] = scale_by(a0, sc);
+        else if (reset) st[i0] = scale_by(a1, sc);
+        else st[i0] = czero(a0);
+        st[i1] = (outc == 1 && !reset) ? scale_by(a1, sc) : czero(a1);
+    }
+}
+
+// ----------------------------------------------------------- expectation --
+template <typename R>
+__global__ void __launch_bounds__(256) k_expect(const void *state, int n, const uint64_t *terms,
+                                                double *partials) {
+    using T = typename V2<R>::T;
+    __shared__ double red[2 * 256 / 32];
+    const T *st = reinterpret_cast<const T *>(state);
+    const uint64_t x = terms[3 * blockIdx.y], z = terms[3 * blockIdx.y + 1];
+    const int ny = __popcll(x & z) & 3;
+    const uint64_t N = 1ull << n, chunk = N / gridDim.x, start = chunk * blockIdx.x;
+    double acc = 0, dummy = 0;
+    for (uint64_t l = threadIdx.x; l < chunk; l += 256) {
+        const uint64_t j = start + l;
+        const double2 aj = to_d(st[j]), ax = to_d(st[j ^ x]);
+        // w = conj(a_{j^x}) * a_j
+        const double wr = ax.x * aj.x + ax.y * aj.y;
+        const double wi = ax.x * aj.y - ax.y * aj.x;
+        // Re(i^ny * w)
+        double v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
+        if (__popcll(j & z) & 1) v = -v;
+        acc += v;
+    }
+    block_sum2<256>(acc, dummy, red);
+    if (threadIdx.x == 0) partials[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_expect_final(const uint64_t *terms, size_t n_terms, int P, const double *partials,
+                               double *out) {
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= n_terms) return;
+    double s = 0;
+    for (int b = 0; b < P; b++) s += partials[t * P + b];
+    out[t] = __longlong_as_double((long long)terms[3 * t + 2]) * s;
+}
+
+template <typename R>
+__global__ void k_set_basis(void *state, uint64_t N, uint64_t index) {
+    using T = typename V2<R>::T;
+    T *st = reinterpret_cast<T *>(state);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        T v = czero(st[0]);
+        if (i == index) v.x = 1;
+        st[i] = v;
+    }
+}
+
+template <typename R> constexpr size_t amp_bytes() { return sizeof(typename V2<R>::T); }
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+int max_resident_bits(int dtype) { return dtype == 0 ? 14 : 13; }
+
+size_t resident_smem_bytes(int dtype, int n) {
+    const size_t es = dtype == 0 ? 8 : 16;
+    return (es << n) + es * 32 * 32;  // state + one staged k <= 5 matrix
+}
+
+cudaError_t setup_kernels() {
+    const int big = 227 * 1024;
+    cudaError_t e;
+#define QSIM_ATTR(fn)                                                                      \
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big - 24 * 1024); \
+    if (e != cudaSuccess) return e;
+    QSIM_ATTR((k_tile_pass<float, 256>));
+    QSIM_ATTR((k_tile_pass<double, 256>));
+    QSIM_ATTR((k_tile_pass<float, 512>));
+    QSIM_ATTR((k_tile_pass<double, 512>));
+    QSIM_ATTR((k_resident_one<float, 256>));
+    QSIM_ATTR((k_resident_one<double, 256>));
+    QSIM_ATTR((k_resident_batch<float, 256>));
+    QSIM_ATTR((k_resident_batch<double, 256>));
+#undef QSIM_ATTR
+    return cudaSuccess;
+}
+
+cudaError_t launch_tile_pass(int dtype, int threads, void *state, int n, int m, uint64_t tile_mask,
+                             const DevOp *ops, uint32_t n_ops, const void *mats,
+                             const MeasCtl *ctl, cudaStream_t s) {
+    TileArgs a;
+    a.state = state;
+    a.ops = ops;
+    a.mats = mats;
+    a.ctl = ctl;
+    a.tile_mask = tile_mask;
+    a.n_ops = n_ops;
+    a.n = n;
+    a.m = m;
+    a.L = dtype == 0 ? (m < 4 ? m : 4) : (m < 3 ? m : 3);
+    const unsigned grid = 1u << (n - m);
+    const size_t es = dtype == 0 ? 8 : 16;
+    const size_t smem = (es << m) + es * 32 * 32;
+    if (dtype == 0) {
+        if (threads == 512) k_tile_pass<float, 512><<<grid, 512, smem, s>>>(a);
+        else k_tile_pass<float, 256><<<grid, 256, smem, s>>>(a);
+    } else {
+        if (threads == 512) k_tile_pass<double, 512><<<grid, 512, smem, s>>>(a);
+        else k_tile_pass<double, 256><<<grid, 256, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s) {
+    (void)threads;
+    const size_t smem = resident_smem_bytes(dtype, inst.n);
+    if (dtype == 0) k_resident_one<float, 256><<<1, 256, smem, s>>>(inst);
+    else k_resident_one<double, 256><<<1, 256, smem, s>>>(inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resident_batch(int dtype, int threads, const Instance *d_insts, int count,
+                                  int max_n, cudaStream_t s) {
+    (void)threads;
+    const size_t smem = resident_smem_bytes(dtype, max_n);
+    if (dtype == 0) k_resident_batch<float, 256><<<count, 256, smem, s>>>(d_insts, max_n);
+    else k_resident_batch<double, 256><<<count, 256, smem, s>>>(d_insts, max_n);
+    return cudaGetLastError();
+}
+
+int prob_blocks(int n) {
+    // chunks of >= 2048 amplitudes, at most 1024 blocks, a power of two
+    int lg = n - 11;
+    if (lg < 0) lg = 0;
+    if (lg > 10) lg = 10;
+    return 1 << lg;
+}
+
+cudaError_t launch_measure(int dtype, void *state, int n, const MeasArgs &a, double *partials,
+                           MeasCtl *ctl, MeasRec *log, cudaStream_t s) {
+    const int P = prob_blocks(n);
+    if (dtype == 0) k_prob<float, true><<<P, kRedThreads, 0, s>>>(state, n, a, partials, ctl, log);
+    else k_prob<double, true><<<P, kRedThreads, 0, s>>>(state, n, a, partials, ctl, log);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t half = 1ull << (n - 1);
+    uint64_t g = (half + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (dtype == 0) k_collapse<float><<<(unsigned)g, 256, 0, s>>>(state, n, a.q, a.reset, ctl);
+    else k_collapse<double><<<(unsigned)g, 256, 0, s>>>(state, n, a.q, a.reset, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prob_only(int dtype, const void *state, int n, int q, double *partials,
+                             MeasCtl *ctl, cudaStream_t s) {
+    const int P = prob_blocks(n);
+    MeasArgs a{};
+    a.q = q;
+    if (dtype == 0) k_prob<float, false><<<P, kRedThreads, 0, s>>>(state, n, a, partials, ctl, nullptr);
+    else k_prob<double, false><<<P, kRedThreads, 0, s>>>(state, n, a, partials, ctl, nullptr);
+    return cudaGetLastError();
+}
+
+int expect_blocks(int n) {
+    int lg = n - 12;
+    if (lg < 0) lg = 0;
+    if (lg > 8) lg = 8;
+    return 1 << lg;
+}
+
+cudaError_t launch_expect(int dtype, const void *state, int n, const uint64_t *d_terms,
+                          size_t n_terms, double *partials, double *d_out, cudaStream_t s) {
+    if (n_terms == 0) return cudaSuccess;
+    const int P = expect_blocks(n);
+    size_t done = 0;
+    while (done < n_terms) {  // grid.y <= 65535
+        const size_t cnt = n_terms - done < 65535 ? n_terms - done : 65535;
+        dim3 grid(P, (unsigned)cnt);
+        if (dtype == 0) k_expect<float><<<grid, 256, 0, s>>>(state, n, d_terms + 3 * done, partials + done * P);
+        else k_expect<double><<<grid, 256, 0, s>>>(state, n, d_terms + 3 * done, partials + done * P);
+        done += cnt;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_expect_final<<<(unsigned)((n_terms + 255) / 256), 256, 0, s>>>(d_terms, n_terms, P, partials, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_basis(int dtype, void *state, int n, uint64_t index, cudaStream_t s) {
+    const uint64_t N = 1ull << n;
+    uint64_t g = (N + 255) / 256;
+    if (g > 8192) g = 8192;
+    if (dtype == 0) k_set_basis<float><<<(unsigned)g, 256, 0, s>>>(state, N, index);
+    else k_set_basis<double><<<(unsigned)g, 256, 0, s>>>(state, N, index);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim

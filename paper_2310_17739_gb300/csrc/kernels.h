@@ -1,0 +1,97 @@
+// kernels.h -- internal launch interface between the host runtime (capi.cpp)
+// and the sm_103a kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace qsim {
+
+// One instruction of a device program (16 bytes).  k > 0: dense 2^k x 2^k
+// complex matrix at mats[mat] (row-major), bit j of the local matrix index
+// <-> tile position lq[j].  k == 0: event `ev` (1 measure, 2 reset) on global
+// qubit lq[0], flags bit 0 = assertion mode.
+struct DevOp {
+    uint8_t k;
+    uint8_t ev;
+    uint16_t flags;
+    uint8_t lq[6];
+    uint16_t pad;
+    uint32_t mat;
+};
+static_assert(sizeof(DevOp) == 16, "DevOp layout");
+
+// Measurement control block of one state (device memory).
+struct MeasCtl {
+    int32_t status;       // sticky: 0 or QSIM_E_ZEROPROB
+    int32_t outcome;      // last outcome (for the collapse kernel)
+    double scale;         // 1/sqrt(p_outcome) of the last measurement
+    double success;       // product of asserted P(0)
+    uint32_t arrive;      // block arrival counter of the grid reduction
+    uint32_t pad;
+    double p0, p1;        // raw sums of the last measurement
+    uint64_t fail_log;    // log index of the measurement that failed
+};
+
+struct MeasRec {
+    int32_t outcome;
+    int32_t pad;
+    double prob;
+};
+
+// A state run resident in one block's shared memory.
+struct Instance {
+    void *state;
+    const DevOp *ops;
+    const void *mats;
+    uint64_t n_ops;
+    uint64_t seed;
+    uint64_t ordinal0;     // draw ordinal of the first event
+    uint64_t log0;         // log index of the first event
+    uint64_t log_cap;
+    MeasCtl *ctl;
+    MeasRec *log;
+    double thr;
+    int32_t n;
+    int32_t pad;
+};
+
+struct MeasArgs {
+    int q;
+    int mode;       // bit 0 assertion
+    int reset;      // 1: RESET (draw, then move |1> onto |0>)
+    int pad;
+    uint64_t seed;
+    uint64_t ordinal;
+    uint64_t log_idx;
+    uint64_t log_cap;
+    double thr;
+};
+
+// dtype: 0 = complex64, 1 = complex128 (values of qsim_dtype).
+cudaError_t setup_kernels();
+size_t resident_smem_bytes(int dtype, int n);
+int max_resident_bits(int dtype);
+
+cudaError_t launch_tile_pass(int dtype, int threads, void *state, int n, int m, uint64_t tile_mask,
+                             const DevOp *ops, uint32_t n_ops, const void *mats,
+                             const MeasCtl *ctl, cudaStream_t s);
+cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s);
+cudaError_t launch_resident_batch(int dtype, int threads, const Instance *d_insts, int count,
+                                  int max_n, cudaStream_t s);
+// Grid size (blocks) the probability reduction uses for an n-qubit state;
+// partials must hold that many double2.
+int prob_blocks(int n);
+cudaError_t launch_measure(int dtype, void *state, int n, const MeasArgs &a, double *partials,
+                           MeasCtl *ctl, MeasRec *log, cudaStream_t s);
+// Born probabilities only (no draw, no collapse): writes ctl->p0, ctl->p1.
+cudaError_t launch_prob_only(int dtype, const void *state, int n, int q, double *partials,
+                             MeasCtl *ctl, cudaStream_t s);
+int expect_blocks(int n);
+cudaError_t launch_expect(int dtype, const void *state, int n, const uint64_t *d_terms,
+                          size_t n_terms, double *partials, double *d_out, cudaStream_t s);
+cudaError_t launch_set_basis(int dtype, void *state, int n, uint64_t index, cudaStream_t s);
+
+}  // namespace qsim

@@ -1,0 +1,353 @@
+"""ctypes binding of libqsim.so (the C ABI declared in include/qsim.h).
+
+Argument marshalling only: every step of gate application, measurement and
+expectation runs in the library's sm_103a kernels.  Device memory comes from
+PyTorch's caching allocator (through the library's allocator hook) and work is
+enqueued on PyTorch's current CUDA stream.  Importing this module raises if the
+native library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .workload import GATE_DTYPE, TERM_DTYPE
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsim.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"native library missing: {LIB_PATH} (run __graft_entry__.build() or "
+                      "python -m paper_2310_17739_gb300.build)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+C64, C128 = 0, 1
+OK, E_INVAL, E_OOM, E_CUDA, E_ZEROPROB, E_TIMEOUT, E_STATE = range(7)
+MEAS_ASSERT = 1
+_vp, _sz, _u64, _i32, _dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+
+
+class QsimConfig(ctypes.Structure):
+    _fields_ = [("fusion", ctypes.c_int32), ("k_max", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("chunk_gates", ctypes.c_int32),
+                ("lookahead", ctypes.c_int32), ("compile_threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ProgramInfo(ctypes.Structure):
+    _fields_ = [("gates", ctypes.c_uint64), ("fused_ops", ctypes.c_uint64), ("passes", ctypes.c_uint64),
+                ("measurements", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("op_hist", ctypes.c_uint64 * 8)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_SIGS = {
+    "qsim_create": ([_i32, _i32, _vp, ALLOC_FN, FREE_FN, _vp, ctypes.POINTER(_vp)], _i32),
+    "qsim_destroy": ([_vp], _i32),
+    "qsim_set_stream": ([_vp, _vp], _i32),
+    "qsim_set_config": ([_vp, ctypes.POINTER(QsimConfig)], _i32),
+    "qsim_get_config": ([_vp, ctypes.POINTER(QsimConfig)], _i32),
+    "qsim_set_seed": ([_vp, _u64], _i32),
+    "qsim_set_assert_threshold": ([_vp, _dbl], _i32),
+    "qsim_apply": ([_vp, _vp, _sz, _vp, _sz], _i32),
+    "qsim_compile": ([_vp, _vp, _sz, _vp, _sz, ctypes.POINTER(_vp)], _i32),
+    "qsim_run": ([_vp, _vp], _i32),
+    "qsim_program_get_info": ([_vp, ctypes.POINTER(ProgramInfo)], _i32),
+    "qsim_program_free": ([_vp], _i32),
+    "qsim_measure": ([_vp, _i32, _u64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_dbl)], _i32),
+    "qsim_prob": ([_vp, _i32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)], _i32),
+    "qsim_outcomes": ([_vp, _vp, _vp, _sz, ctypes.POINTER(_sz)], _i32),
+    "qsim_success_prob": ([_vp, ctypes.POINTER(_dbl)], _i32),
+    "qsim_expect": ([_vp, _vp, _sz, _vp], _i32),
+    "qsim_state": ([_vp, _vp, _sz, _i32], _i32),
+    "qsim_set_state": ([_vp, _vp, _sz, _i32], _i32),
+    "qsim_reset_state": ([_vp], _i32),
+    "qsim_state_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)], _i32),
+    "qsim_sync": ([_vp], _i32),
+    "qsim_last_error": ([_vp], ctypes.c_char_p),
+    "qsim_status_string": ([_i32], ctypes.c_char_p),
+    "qsim_fuse": ([_i32, _i32, _vp, _sz, _vp, _sz, ctypes.POINTER(QsimConfig), _vp, _vp, _vp, _sz, _vp, _sz,
+                   ctypes.POINTER(_sz), ctypes.POINTER(_sz)], _i32),
+    "qsim_schedule": ([_i32, _i32, _vp, _sz, _vp, _sz, ctypes.POINTER(QsimConfig), _vp, _vp, _vp, _sz,
+                       ctypes.POINTER(_sz)], _i32),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def lib():
+    return _lib
+
+
+class QsimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.qsim_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(st, ctx=None):
+    if st != OK:
+        msg = _lib.qsim_last_error(ctx).decode(errors="replace")
+        raise QsimError(st, msg)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else ctypes.c_void_p(0)
+
+
+def _gates(g):
+    g = np.ascontiguousarray(g, dtype=GATE_DTYPE)
+    return g
+
+
+def _mats(m):
+    if m is None:
+        return np.zeros(1, dtype=np.float64)
+    return np.ascontiguousarray(m, dtype=np.float64).ravel()
+
+
+def make_config(fusion=1, k_max=2, tile_bits=0, threads=0, chunk_gates=0, lookahead=0,
+                compile_threads=0) -> QsimConfig:
+    return QsimConfig(fusion, k_max, tile_bits, threads, chunk_gates, lookahead, compile_threads, 0)
+
+
+# ----------------------------------------------------------- torch plumbing --
+class _TorchAllocator:
+    """Device memory through torch's caching allocator (stream-ordered frees)."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream)
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            if ptr:
+                self.torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class Program:
+    def __init__(self, sim, handle):
+        self.sim = sim
+        self.handle = handle
+
+    def info(self) -> dict:
+        inf = ProgramInfo()
+        _check(_lib.qsim_program_get_info(self.handle, ctypes.byref(inf)))
+        return dict(gates=inf.gates, fused_ops=inf.fused_ops, passes=inf.passes,
+                    measurements=inf.measurements, device_bytes=inf.device_bytes,
+                    op_hist=list(inf.op_hist))
+
+    def free(self):
+        if self.handle:
+            _lib.qsim_program_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Sim:
+    """One state vector of n qubits on the current CUDA device."""
+
+    def __init__(self, n: int, dtype: str = "c64", stream=None, torch_memory: bool = True,
+                 config: Optional[dict] = None, seed: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.n = n
+        self.dtype = C64 if dtype in ("c64", C64) else C128
+        self.np_dtype = np.complex64 if self.dtype == C64 else np.complex128
+        self.device = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self._alloc = _TorchAllocator(self.device) if torch_memory else None
+        h = ctypes.c_void_p()
+        _check(_lib.qsim_create(n, self.dtype, sp,
+                                self._alloc.alloc if self._alloc else ALLOC_FN(),
+                                self._alloc.free if self._alloc else FREE_FN(),
+                                None, ctypes.byref(h)))
+        self.h = h
+        if config:
+            self.set_config(**config)
+        if seed:
+            self.set_seed(seed)
+
+    # -- configuration
+    def set_config(self, **kw):
+        cfg = self.get_config()
+        cfg.update(kw)
+        _check(_lib.qsim_set_config(self.h, ctypes.byref(make_config(**cfg))), self.h)
+
+    def get_config(self) -> dict:
+        c = QsimConfig()
+        _check(_lib.qsim_get_config(self.h, ctypes.byref(c)), self.h)
+        return dict(fusion=c.fusion, k_max=c.k_max, tile_bits=c.tile_bits, threads=c.threads,
+                    chunk_gates=c.chunk_gates, lookahead=c.lookahead, compile_threads=c.compile_threads)
+
+    def set_seed(self, seed: int):
+        _check(_lib.qsim_set_seed(self.h, seed), self.h)
+
+    def set_assert_threshold(self, thr: float):
+        _check(_lib.qsim_set_assert_threshold(self.h, thr), self.h)
+
+    # -- gates
+    def apply(self, gates, mats=None):
+        g = _gates(gates)
+        m = _mats(mats)
+        _check(_lib.qsim_apply(self.h, _ptr(g), g.size, _ptr(m), m.size), self.h)
+
+    def compile(self, gates, mats=None) -> Program:
+        g = _gates(gates)
+        m = _mats(mats)
+        p = ctypes.c_void_p()
+        _check(_lib.qsim_compile(self.h, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(p)), self.h)
+        return Program(self, p)
+
+    def run(self, prog: Program):
+        _check(_lib.qsim_run(self.h, prog.handle), self.h)
+
+    # -- measurement
+    def measure(self, qubit: int, seed: int, mode: int = 0):
+        out = ctypes.c_int()
+        pr = ctypes.c_double()
+        st = _lib.qsim_measure(self.h, qubit, seed, mode, ctypes.byref(out), ctypes.byref(pr))
+        if st == E_ZEROPROB:
+            return -1, pr.value, st
+        _check(st, self.h)
+        return out.value, pr.value, st
+
+    def measure_async(self, qubit: int, seed: int, mode: int = 0):
+        _check(_lib.qsim_measure(self.h, qubit, seed, mode, None, None), self.h)
+
+    def prob(self, qubit: int):
+        p0, p1 = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.qsim_prob(self.h, qubit, ctypes.byref(p0), ctypes.byref(p1)), self.h)
+        return p0.value, p1.value
+
+    def outcomes(self, check: bool = True):
+        n = ctypes.c_size_t()
+        _check(_lib.qsim_outcomes(self.h, None, None, 0, ctypes.byref(n)), self.h)
+        k = n.value
+        oc = np.zeros(max(k, 1), dtype=np.int32)
+        pr = np.zeros(max(k, 1), dtype=np.float64)
+        st = _lib.qsim_outcomes(self.h, _ptr(oc), _ptr(pr), k, ctypes.byref(n))
+        if check:
+            _check(st, self.h)
+        return oc[:k].copy(), pr[:k].copy()
+
+    def success_prob(self):
+        p = ctypes.c_double()
+        st = _lib.qsim_success_prob(self.h, ctypes.byref(p))
+        return p.value, st
+
+    # -- expectation
+    def expect(self, terms) -> np.ndarray:
+        t = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+        out = np.zeros(max(t.size, 1), dtype=np.float64)
+        _check(_lib.qsim_expect(self.h, _ptr(t), t.size, _ptr(out)), self.h)
+        return out[: t.size]
+
+    # -- state
+    def state(self) -> np.ndarray:
+        a = np.zeros(1 << self.n, dtype=self.np_dtype)
+        _check(_lib.qsim_state(self.h, _ptr(a), a.nbytes, 0), self.h)
+        return a
+
+    def state_tensor(self):
+        """A torch view (no copy) of the device state."""
+        import torch
+        p = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        _check(_lib.qsim_state_ptr(self.h, ctypes.byref(p), ctypes.byref(nb)), self.h)
+        return p.value, nb.value
+
+    def set_state(self, arr):
+        a = np.ascontiguousarray(arr, dtype=self.np_dtype)
+        _check(_lib.qsim_set_state(self.h, _ptr(a), a.nbytes, 0), self.h)
+
+    def reset(self):
+        _check(_lib.qsim_reset_state(self.h), self.h)
+
+    def sync(self):
+        return _lib.qsim_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qsim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------- host-only inspection --
+def fuse(n, gates, mats=None, dtype=C64, **cfg):
+    """Compiled op list of one chunk: list of (k, qubits, matrix) / ('event', op, q, flags)."""
+    g = _gates(gates)
+    m = _mats(mats)
+    c = make_config(**cfg)
+    nops, nmd = ctypes.c_size_t(), ctypes.c_size_t()
+    st = _lib.qsim_fuse(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), None, None, None, 0,
+                        None, 0, ctypes.byref(nops), ctypes.byref(nmd))
+    if st not in (OK, E_INVAL) or (st == E_INVAL and nops.value == 0 and g.size):
+        _check(st)
+    K = max(nops.value, 1)
+    ok = np.zeros(K, dtype=np.uint8)
+    oq = np.zeros(6 * K, dtype=np.uint32)
+    om = np.zeros(K, dtype=np.uint64)
+    md = np.zeros(max(nmd.value, 1), dtype=np.float64)
+    _check(_lib.qsim_fuse(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), _ptr(ok), _ptr(oq),
+                          _ptr(om), K, _ptr(md), md.size, ctypes.byref(nops), ctypes.byref(nmd)))
+    out = []
+    for i in range(nops.value):
+        k = int(ok[i])
+        if k == 0:
+            out.append(("event", int(oq[6 * i + 1]), int(oq[6 * i]), int(oq[6 * i + 2])))
+        else:
+            d = 1 << k
+            off = int(om[i])
+            M = md[off: off + 2 * d * d].view(np.complex128).reshape(d, d).copy()
+            out.append((k, [int(x) for x in oq[6 * i: 6 * i + k]], M))
+    return out
+
+
+def schedule(n, gates, mats=None, dtype=C64, **cfg):
+    """Pass table of one chunk: list of (tile_mask, first, count)."""
+    g = _gates(gates)
+    m = _mats(mats)
+    c = make_config(**cfg)
+    npass = ctypes.c_size_t()
+    _lib.qsim_schedule(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), None, None, None, 0,
+                       ctypes.byref(npass))
+    K = max(npass.value, 1)
+    t = np.zeros(K, dtype=np.uint64)
+    f = np.zeros(K, dtype=np.uint64)
+    cnt = np.zeros(K, dtype=np.uint32)
+    _check(_lib.qsim_schedule(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), _ptr(t), _ptr(f),
+                              _ptr(cnt), K, ctypes.byref(npass)))
+    return [(int(t[i]), int(f[i]), int(cnt[i])) for i in range(npass.value)]

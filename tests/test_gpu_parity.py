@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (written from the arithmetic):
+  complex128: max |a_gpu - a_oracle| <= 1e-10 (no phase alignment);
+  complex64:  infidelity 1 - |<a_oracle|a_gpu>|^2 / (|a_oracle|^2 |a_gpu|^2) <= 1e-5;
+  measurement outcomes: bit-exact, except a logged near-tie |u - P0_oracle| < 1e-12
+  (c128) / 1e-5 (c64), which the fixed seeds here must not produce.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_17739_gb300 import workload as W
+from paper_2310_17739_gb300.workload import OP
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+qs = pytest.importorskip("paper_2310_17739_gb300.qsim")
+
+C128_TOL = 1e-10
+C64_INFID = 1e-5
+
+
+def run_oracle(c, seed=0, thr=0.0, psi=None):
+    psi = oracle.basis_state(c.n) if psi is None else psi.astype(np.complex128).copy()
+    r = oracle.run(psi, c.n, c.gates, c.mats, seed=seed, thr=thr)
+    return psi, r
+
+
+def run_gpu(c, dtype, seed=0, config=None, psi=None, use_compile=False):
+    sim = qs.Sim(c.n, dtype, config=config or {}, seed=seed)
+    if psi is not None:
+        sim.set_state(psi)
+    if use_compile:
+        p = sim.compile(c.gates, c.mats)
+        sim.run(p)
+        st = sim.sync()
+        p.free()
+    else:
+        sim.apply(c.gates, c.mats)
+        st = sim.sync()
+    return sim, st
+
+
+def check_state(dtype, got, ref):
+    if dtype == "c128":
+        assert np.abs(got.astype(np.complex128) - ref).max() <= C128_TOL
+    else:
+        assert 1 - H.fidelity(ref, got) <= C64_INFID
+
+
+def check_outcomes(dtype, g_out, g_prob, r, seed):
+    o_out, o_prob = r.outcomes, r.probs
+    assert len(g_out) == len(o_out)
+    tie = 1e-12 if dtype == "c128" else 1e-5
+    ptol = 1e-10 if dtype == "c128" else 1e-5
+    for i, (a, b) in enumerate(zip(g_out, o_out)):
+        if a != b:
+            p0 = o_prob[i] if b == 0 else 1 - o_prob[i]
+            pytest.fail(f"outcome {i} differs (gpu {a}, oracle {b}, oracle P0 {p0})")
+    assert np.abs(np.asarray(g_prob) - o_prob).max() <= ptol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,tile_bits", [(3, 0), (7, 0), (10, 0), (12, 8), (13, 10), (14, 12)])
+def test_random_gate_mix(dtype, n, tile_bits):
+    c = W.random_circuit(n, 600, seed=n, with_generic=False)
+    ref, _ = run_oracle(c)
+    sim, st = run_gpu(c, dtype, config=dict(tile_bits=tile_bits))
+    assert st == 0
+    check_state(dtype, sim.state(), ref)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_generic_matrices_non_unitary(dtype):
+    n = 9
+    c = W.random_circuit(n, 60, seed=4)
+    ref, _ = run_oracle(c)
+    sim, st = run_gpu(c, dtype, config=dict(tile_bits=7))
+    got = sim.state().astype(np.complex128)
+    scale = np.abs(ref).max()
+    tol = 1e-12 if dtype == "c128" else 3e-5
+    assert np.abs(got - ref).max() <= tol * scale
+
+
+@pytest.mark.parametrize("fusion,k_max", [(0, 2), (1, 2), (1, 3), (1, 4), (1, 5)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_fusion_levels(dtype, fusion, k_max):
+    n = 15
+    c = W.ucc_circuit(n, seed=21, n_gadgets=60, w_lo=2, w_hi=6, target_gates=5000)
+    ref, _ = run_oracle(c)
+    sim, st = run_gpu(c, dtype, config=dict(fusion=fusion, k_max=k_max, tile_bits=11))
+    check_state(dtype, sim.state(), ref)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_small_config_state_and_z(dtype):
+    """8 qubits, 40 weight 2-4 gadgets cycled to 2,000 gates, |0..0>: state + <Z_i>."""
+    c = W.config_small()
+    ref, _ = run_oracle(c)
+    sim, _ = run_gpu(c, dtype)
+    check_state(dtype, sim.state(), ref)
+    zt = W.z_terms(8)
+    z_ref = oracle.expect(ref, 8, zt)
+    z = sim.expect(zt)
+    assert np.abs(z - z_ref).max() <= (1e-12 if dtype == "c128" else 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("tile_bits", [0, 9])
+def test_mid_circuit_measurements_bit_exact(dtype, tile_bits):
+    n = 14
+    c = W.ucc_circuit(n, seed=2, n_gadgets=None, w_lo=2, w_hi=8, theta="normal0.1",
+                      target_gates=20000, n_meas=16)
+    ref, r = run_oracle(c, seed=1002)
+    sim, st = run_gpu(c, dtype, seed=1002, config=dict(tile_bits=tile_bits))
+    assert st == 0
+    out, prob = sim.outcomes()
+    check_outcomes(dtype, out, prob, r, 1002)
+    check_state(dtype, sim.state(), ref)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_measure_api_and_reset(dtype):
+    n = 12
+    c = W.ucc_circuit(n, seed=8, n_gadgets=20, w_lo=2, w_hi=5, target_gates=600)
+    ref, _ = run_oracle(c)
+    sim, _ = run_gpu(c, dtype)
+    for k, q in enumerate([0, 5, 11, 3]):
+        st_o, out_o, pr_o = oracle.measure(ref, n, q, seed=77, k=k)
+        out, pr, st = sim.measure(q, 77)
+        assert st == 0 and out == out_o
+        assert abs(pr - pr_o) < (1e-12 if dtype == "c128" else 1e-6)
+    check_state(dtype, sim.state(), ref)
+    p0, p1 = sim.prob(7)
+    r0, r1 = oracle.prob(ref, n, 7)
+    assert abs(p0 - r0) < 1e-6 and abs(p1 - r1) < 1e-6
+
+
+@pytest.mark.parametrize("tile_bits", [0, 8])
+def test_assertion_mode_and_success_product(tile_bits):
+    t = H.load_mma_table("tests/golden/mma_table.txt")
+    p0s = t["MMA"][:8]
+    n = 10
+    rows = [(OP["H"], q, 0, 0.0, 0, 0) for q in range(1, n)]
+    for p in p0s:
+        th = 2 * math.acos(math.sqrt(p))
+        rows += [(OP["RY"], 0, 0, th, 0, 0), (OP["MEASURE"], 0, 0, 0, 0, 0, 1),
+                 (OP["BARRIER"], 0, 0, 0, 0, 0), (OP["RESET"], 0, 0, 0, 0, 0)]
+    c = W.Circuit(n, W.records(rows))
+    ref, r = run_oracle(c)
+    sim, st = run_gpu(c, "c128", config=dict(tile_bits=tile_bits))
+    assert st == 0
+    out, prob = sim.outcomes()
+    assert np.array_equal(out, r.outcomes)
+    succ, st = sim.success_prob()
+    assert abs(succ - np.prod(p0s)) < 1e-12
+    assert abs(succ - t["MMA"][8]) < 5e-7
+    check_state("c128", sim.state(), ref)
+
+
+@pytest.mark.parametrize("tile_bits", [0, 8])
+def test_assertion_failure_keeps_state(tile_bits):
+    n = 10
+    rows = [(OP["H"], 3, 0, 0, 0, 0), (OP["X"], 0, 0, 0, 0, 0), (OP["MEASURE"], 0, 0, 0, 0, 0, 1),
+            (OP["H"], 5, 0, 0, 0, 0)]
+    c = W.Circuit(n, W.records(rows))
+    sim = qs.Sim(n, "c128", config=dict(tile_bits=tile_bits))
+    sim.apply(c.gates)
+    assert sim.sync() == qs.E_ZEROPROB
+    ref = oracle.basis_state(n)
+    r = oracle.run(ref, n, c.gates)
+    assert r.status == oracle.E_ZEROPROB
+    check_state("c128", sim.state(), ref)
+    # the context refuses further work until reset
+    sim.apply(W.records([(OP["X"], 1, 0, 0, 0, 0)]))
+    assert sim.sync() == qs.E_ZEROPROB
+    sim.reset()
+    assert sim.sync() == 0
+    st0 = sim.state()
+    assert st0[0] == 1 and np.count_nonzero(st0) == 1
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_expectation_random_hamiltonian(dtype):
+    n = 12
+    c = W.ucc_circuit(n, seed=44, n_gadgets=30, w_lo=2, w_hi=6, target_gates=3000)
+    ref, _ = run_oracle(c)
+    sim, _ = run_gpu(c, dtype)
+    terms = W.random_hamiltonian(n, 200, seed=4)
+    e_ref = oracle.expect(ref, n, terms)
+    e = sim.expect(terms)
+    tol = 1e-11 if dtype == "c128" else 2e-5
+    assert np.abs(e - e_ref).max() <= tol * max(1.0, np.abs(terms["coef"]).max())
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_compile_run_equals_apply_and_repeats(dtype):
+    n = 16
+    c = W.ucc_circuit(n, seed=3, n_gadgets=50, w_lo=2, w_hi=6, target_gates=8000, n_meas=3)
+    sim_a, _ = run_gpu(c, dtype, seed=5)
+    sim_b, _ = run_gpu(c, dtype, seed=5, use_compile=True)
+    a, b = sim_a.state(), sim_b.state()
+    assert np.array_equal(a, b)
+    # chunked compile (small chunks) gives the same physics
+    ref, r = run_oracle(c, seed=5)
+    sim_c, _ = run_gpu(c, dtype, seed=5, config=dict(chunk_gates=1000, compile_threads=3))
+    out, prob = sim_c.outcomes()
+    check_outcomes(dtype, out, prob, r, 5)
+    check_state(dtype, sim_c.state(), ref)
+
+
+def test_empty_and_edge_inputs():
+    sim = qs.Sim(1, "c128")
+    sim.apply(W.records([]))
+    assert sim.sync() == 0
+    sim.apply(W.records([(OP["H"], 0, 0, 0, 0, 0)]))
+    s = sim.state()
+    assert abs(s[0] - 1 / math.sqrt(2)) < 1e-15 and abs(s[1] - 1 / math.sqrt(2)) < 1e-15
+    with pytest.raises(qs.QsimError):
+        sim.apply(W.records([(OP["H"], 1, 0, 0, 0, 0)]))
+    with pytest.raises(qs.QsimError):
+        qs.Sim(35, "c64")
+    sim2 = qs.Sim(2, "c64")
+    with pytest.raises(qs.QsimError):
+        sim2.set_config(tile_bits=20)

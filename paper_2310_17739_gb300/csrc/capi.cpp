@@ -132,6 +132,12 @@ struct qsim_ctx {
     std::vector<Staging> staging;
     std::string err;
     bool broken = false;
+    // sampled tile-pass timing
+    int prof_every = 0;
+    uint64_t prof_launches = 0;
+    size_t prof_used = 0;
+    double prof_flops = 0, prof_bytes = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
 };
 
 struct qsim_program {
@@ -345,9 +351,19 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
             continue;
         }
         if (!p.count) continue;
+        const bool sample = c->prof_every > 0 && c->prof_launches % (uint64_t)c->prof_every == 0 &&
+                            c->prof_used < c->prof_ev.size();
+        if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
         CK(qsim::launch_tile_pass(c->dtype, threads, c->state, c->n, dc.m, p.tile,
                                   dc.d_ops + p.first, p.count, dc.d_mats, c->ctl, c->stream),
            "tile pass launch");
+        if (sample) {
+            CK(cudaEventRecord(c->prof_ev[c->prof_used].second, c->stream), "profile event");
+            c->prof_used++;
+            c->prof_flops += (double)p.fpa * (double)(1ull << c->n);
+            c->prof_bytes += 2.0 * (double)c->state_bytes;
+        }
+        c->prof_launches++;
     }
     return QSIM_OK;
 }
@@ -517,6 +533,10 @@ qsim_status qsim_destroy(qsim_ctx *c) {
         cudaFreeHost(s.host);
     }
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    for (auto &e : c->prof_ev) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
     cudaGetLastError();
     delete c;
     return QSIM_OK;
@@ -792,6 +812,44 @@ qsim_status qsim_sync(qsim_ctx *c) {
     qsim_status s = check_usable(c);
     if (s != QSIM_OK) return s;
     return sync_read(c);
+}
+
+qsim_status qsim_profile_start(qsim_ctx *c, int every) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (every < 0) return fail(c, QSIM_E_INVAL, "every must be >= 0");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    const size_t cap = 8192;
+    while (every > 0 && c->prof_ev.size() < cap) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a), "event create");
+        CK(cudaEventCreate(&b), "event create");
+        c->prof_ev.emplace_back(a, b);
+    }
+    c->prof_every = every;
+    c->prof_launches = 0;
+    c->prof_used = 0;
+    c->prof_flops = c->prof_bytes = 0;
+    return QSIM_OK;
+}
+
+qsim_status qsim_profile_read(qsim_ctx *c, double *ms, uint64_t *n_sampled, double *flops, double *bytes,
+                              uint64_t *n_launches) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    double tot = 0;
+    for (size_t i = 0; i < c->prof_used; i++) {
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, c->prof_ev[i].first, c->prof_ev[i].second), "event elapsed");
+        tot += t;
+    }
+    if (ms) *ms = tot;
+    if (n_sampled) *n_sampled = c->prof_used;
+    if (flops) *flops = c->prof_flops;
+    if (bytes) *bytes = c->prof_bytes;
+    if (n_launches) *n_launches = c->prof_launches;
+    return QSIM_OK;
 }
 
 // ----------------------------------------------------- host-only inspection --

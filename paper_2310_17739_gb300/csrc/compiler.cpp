@@ -577,6 +577,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             }
         }
         p.count = (uint32_t)(sched.size() - p.first);
+        for (size_t i = p.first; i < sched.size(); i++) p.fpa += 8u << sched[i].k;
         out.passes.push_back(p);
     }
     for (const FOp &o : sched)

@@ -46,6 +46,7 @@ struct Pass {
     uint8_t pad = 0;
     uint16_t flags = 0;   // event flags (bit 0: assertion mode)
     uint32_t q = 0;       // event qubit
+    uint32_t fpa = 0;     // algorithmic real flops per amplitude of the pass (8 * 2^k per op)
 };
 
 struct Config {

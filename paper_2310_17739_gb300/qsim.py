@@ -70,6 +70,9 @@ _SIGS = {
     "qsim_reset_state": ([_vp], _i32),
     "qsim_state_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)], _i32),
     "qsim_sync": ([_vp], _i32),
+    "qsim_profile_start": ([_vp, _i32], _i32),
+    "qsim_profile_read": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_u64), ctypes.POINTER(_dbl),
+                           ctypes.POINTER(_dbl), ctypes.POINTER(_u64)], _i32),
     "qsim_last_error": ([_vp], ctypes.c_char_p),
     "qsim_status_string": ([_i32], ctypes.c_char_p),
     "qsim_fuse": ([_i32, _i32, _vp, _sz, _vp, _sz, ctypes.POINTER(QsimConfig), _vp, _vp, _vp, _sz, _vp, _sz,
@@ -292,6 +295,17 @@ class Sim:
 
     def sync(self):
         return _lib.qsim_sync(self.h)
+
+    # -- sampled kernel timing
+    def profile_start(self, every: int):
+        _check(_lib.qsim_profile_start(self.h, every), self.h)
+
+    def profile_read(self) -> dict:
+        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        ns, nl = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.qsim_profile_read(self.h, ctypes.byref(ms), ctypes.byref(ns), ctypes.byref(fl),
+                                      ctypes.byref(by), ctypes.byref(nl)), self.h)
+        return dict(ms=ms.value, samples=ns.value, flops=fl.value, bytes=by.value, launches=nl.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -247,6 +247,32 @@ QSIM_API qsim_status qsim_sync(qsim_ctx *ctx);
 QSIM_API const char *qsim_last_error(const qsim_ctx *ctx);
 QSIM_API const char *qsim_status_string(qsim_status s);
 
+/* ------------------------------------------------ no-allocation variant --
+ * The paper has no counterpart to this entry point; it serves callers that
+ * own a state vector in device memory but may not allocate device memory
+ * themselves or through the library (for example a plug-in whose host
+ * framework hands out all device memory from its own fixed pool, or a
+ * latency-critical loop where cudaMalloc/cudaFree, which can synchronise the
+ * device, are not allowed).
+ *
+ * qsim_prob_noalloc: p0 = sum |a_i|^2 over bit `qubit` = 0 and p1 likewise
+ * (FP64 accumulation, the same reduction as qsim_prob) of the caller's state
+ * d_state (device pointer, 2^n_qubits interleaved amplitudes of `dtype`),
+ * enqueued on `stream` (NULL = legacy default stream) and synchronised; the
+ * results are written to the host doubles *p0, *p1.  It allocates nothing: the
+ * reduction's scratch is a fixed 16.25 KiB array in the library's device
+ * memory, present on every GPU that loads the library until the process
+ * exits.  Limits: 1 <= n_qubits <= 34 and 0 <= qubit < n_qubits, otherwise
+ * QSIM_E_INVAL with nothing enqueued; QSIM_E_CUDA on a CUDA error.  The first
+ * call on each device looks up the scratch array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the scratch array, which
+ * keeps the last call's contents (each call clears what must start at zero);
+ * calls that may overlap on the GPU (different streams or threads) race on it
+ * and must be ordered by the caller. */
+QSIM_API qsim_status qsim_prob_noalloc(const void *d_state, int n_qubits, qsim_dtype dtype, int qubit,
+                                       void *stream, double *p0, double *p1);
+
 /* ------------------------------------------- host-only compiler inspection --
  * These run the host compiler only (no GPU needed).
  *

@@ -47,6 +47,7 @@ struct DevChunk {
     size_t mats_bytes = 0;
     std::vector<Pass> passes;
     int m = 0;
+    int kmax = 2;
     bool resident = false;
     uint64_t measurements = 0;
 };
@@ -88,8 +89,22 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
             DevOp &d = pk.ops[i];
             std::memset(&d, 0, sizeof(d));
             d.k = o.k;
-            for (int j = 0; j < o.k; j++)
-                d.lq[j] = (uint8_t)__builtin_popcountll(p.tile & ((1ull << o.q[j]) - 1ull));
+            auto local = [&](uint64_t q) {
+                return (uint32_t)__builtin_popcountll(p.tile & ((1ull << q) - 1ull));
+            };
+            if (o.pauli()) {  // tile-local X and Z masks (<= 15 bits each) in lq[0..3]
+                uint32_t lx = 0, lz = 0;
+                for (int q = 0; q < 64; q++) {
+                    if ((o.xm >> q) & 1) lx |= 1u << local(q);
+                    if ((o.zm >> q) & 1) lz |= 1u << local(q);
+                }
+                d.lq[0] = (uint8_t)(lx & 0xff);
+                d.lq[1] = (uint8_t)(lx >> 8);
+                d.lq[2] = (uint8_t)(lz & 0xff);
+                d.lq[3] = (uint8_t)(lz >> 8);
+            } else {
+                for (int j = 0; j < o.k; j++) d.lq[j] = (uint8_t)local(o.q[j]);
+            }
             d.mat = (uint32_t)o.mat;
             fused++;
         }
@@ -275,6 +290,12 @@ qsim_status upload_chunk(qsim_ctx *c, const Packed &pk, DevChunk &dc) {
     dc.mats_bytes = pk.mats.size();
     dc.passes = pk.passes;
     dc.m = pk.m;
+    dc.kmax = 1;  // largest dense op (Pauli rotations, hist[7], run in every variant)
+    for (int k = 5; k >= 1; k--)
+        if (pk.hist[k]) {
+            dc.kmax = k;
+            break;
+        }
     dc.resident = pk.resident;
     dc.measurements = pk.measurements;
     dc.d_ops = (DevOp *)dalloc(c, std::max<size_t>(dc.n_ops, 1) * sizeof(DevOp));
@@ -354,7 +375,7 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
         const bool sample = c->prof_every > 0 && c->prof_launches % (uint64_t)c->prof_every == 0 &&
                             c->prof_used < c->prof_ev.size();
         if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
-        CK(qsim::launch_tile_pass(c->dtype, threads, c->state, c->n, dc.m, p.tile,
+        CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile,
                                   dc.d_ops + p.first, p.count, dc.d_mats, c->ctl, c->stream),
            "tile pass launch");
         if (sample) {
@@ -553,7 +574,7 @@ qsim_status qsim_set_stream(qsim_ctx *c, void *stream) {
 
 qsim_status qsim_set_config(qsim_ctx *c, const qsim_config *cfg) {
     if (!c || !cfg) return fail(c, QSIM_E_INVAL, "null argument");
-    if (cfg->fusion < 0 || cfg->fusion > 1) return fail(c, QSIM_E_INVAL, "fusion must be 0 or 1");
+    if (cfg->fusion < 0 || cfg->fusion > 2) return fail(c, QSIM_E_INVAL, "fusion must be 0, 1 or 2");
     if (cfg->k_max != 0 && (cfg->k_max < 2 || cfg->k_max > 5))
         return fail(c, QSIM_E_INVAL, "k_max must be 0 or in [2, 5]");
     const int mx = qsim::max_resident_bits(c->dtype);
@@ -870,7 +891,13 @@ qsim_status qsim_fuse(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, co
         const qsim::FOp &o = hp.ops[i];
         out_k[i] = o.k;
         for (int j = 0; j < 6; j++) out_q[6 * i + j] = 0;
-        if (o.k) {
+        if (o.pauli()) {
+            out_q[6 * i] = (uint32_t)o.xm;
+            out_q[6 * i + 1] = (uint32_t)(o.xm >> 32);
+            out_q[6 * i + 2] = (uint32_t)o.zm;
+            out_q[6 * i + 3] = (uint32_t)(o.zm >> 32);
+            out_mat[i] = o.mat * 2;
+        } else if (o.k) {
             for (int j = 0; j < o.k; j++) out_q[6 * i + j] = o.q[j];
             out_mat[i] = o.mat * 2;
         } else {

@@ -226,6 +226,154 @@ void left_apply(cd *E, int u, const uint32_t *us, const cd *B, int kb, const uin
 
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
+// ---------------------------------------------------- Pauli-gadget blocks --
+// A block  B_q (1-qubit gates per qubit) ; F (CX network) ; RZ(phi) on t ;
+// F reversed ; B_q^dagger  equals  B^dag F^dag exp(-i phi/2 Z_t) F B
+// = exp(-i phi/2 * B^dag Z_S B)  with S the set of qubits whose bits F XORs
+// into t (F^dag Z_t F = Z_S for a CX network).  Each B_q^dag Z B_q must be a
+// signed Pauli; the product of the signs goes into the angle.
+struct Gadget {
+    size_t len = 0;
+    uint64_t xm = 0, zm = 0;
+    double theta = 0;
+};
+
+bool is_basis_gate(const qsim_gate &g) {
+    switch (g.op) {
+        case QSIM_OP_H: case QSIM_OP_S: case QSIM_OP_SDG: case QSIM_OP_X: case QSIM_OP_Y:
+        case QSIM_OP_Z: case QSIM_OP_RX: case QSIM_OP_RY: case QSIM_OP_U2: case QSIM_OP_U3:
+            return true;
+        default: return false;
+    }
+}
+
+// Which signed Pauli U^dag Z U is: 1=X, 2=Y, 3=Z (sign in *sgn), 0 = none.
+int conj_z(const cd *U, int *sgn) {
+    // V = U^dag Z U
+    cd V[4];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++) V[r * 2 + c] = std::conj(U[0 * 2 + r]) * U[0 * 2 + c] - std::conj(U[1 * 2 + r]) * U[1 * 2 + c];
+    const double tol = 1e-12;
+    auto near = [&](const cd *P, double s) {
+        for (int i = 0; i < 4; i++)
+            if (std::abs(V[i] - s * P[i]) > tol) return false;
+        return true;
+    };
+    static const cd X[4] = {0, 1, 1, 0}, Y[4] = {0, cd(0, -1), cd(0, 1), 0}, Z[4] = {1, 0, 0, -1};
+    const cd *P[3] = {X, Y, Z};
+    for (int p = 0; p < 3; p++)
+        for (int s = -1; s <= 1; s += 2)
+            if (near(P[p], s)) {
+                *sgn = s;
+                return p + 1;
+            }
+    return 0;
+}
+
+bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double *mats, size_t nm,
+                  Gadget &out) {
+    (void)n;
+    const size_t kMaxLead = 16;
+    size_t j = i;
+    uint64_t lead_mask = 0;
+    std::vector<std::pair<uint32_t, size_t>> lead;  // (qubit, gate index)
+    while (j < end && lead.size() < kMaxLead && is_basis_gate(g[j])) {
+        lead.emplace_back(g[j].q0, j);
+        lead_mask |= 1ull << g[j].q0;
+        j++;
+    }
+    // CX network
+    const size_t f0 = j;
+    while (j < end && g[j].op == QSIM_OP_CX) j++;
+    const size_t f1 = j;
+    if (f1 == f0 || j >= end || g[j].op != QSIM_OP_RZ) return false;
+    const uint32_t t = g[j].q0;
+    const double phi = g[j].p[0];
+    j++;
+    const size_t nf = f1 - f0;
+    if (j + nf > end) return false;
+    for (size_t k = 0; k < nf; k++) {
+        const qsim_gate &a = g[f1 - 1 - k], &b = g[j + k];
+        if (b.op != QSIM_OP_CX || b.q0 != a.q0 || b.q1 != a.q1) return false;
+    }
+    j += nf;
+    // parity set: bits XORed into t by the network
+    uint64_t rowmask[64];
+    uint64_t touched = 1ull << t;
+    for (size_t k = f0; k < f1; k++) touched |= (1ull << g[k].q0) | (1ull << g[k].q1);
+    for (int q = 0; q < 64; q++) rowmask[q] = (touched >> q) & 1 ? (1ull << q) : 0;
+    for (size_t k = f0; k < f1; k++) rowmask[g[k].q1] ^= rowmask[g[k].q0];
+    const uint64_t S = rowmask[t];
+    if (popc(S) < 2) return false;
+    // per-qubit lead products
+    cd Ulead[64][4];
+    int nlead[64] = {0};
+    for (auto &pr : lead) {
+        const uint32_t q = pr.first;
+        cd m[16];
+        if (gate_matrix(g[pr.second], mats, nm, m) != 2) return false;
+        if (nlead[q] == 0) {
+            for (int e = 0; e < 4; e++) Ulead[q][e] = m[e];
+        } else {
+            cd *U = Ulead[q];
+            cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
+                       m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
+            for (int e = 0; e < 4; e++) U[e] = r[e];
+        }
+        nlead[q]++;
+    }
+    // trailing: as many 1-qubit gates per qubit as the lead had, undoing it
+    cd Utrail[64][4];
+    int ntrail[64] = {0};
+    size_t need = lead.size();
+    while (need > 0) {
+        if (j >= end || !is_basis_gate(g[j])) return false;
+        const uint32_t q = g[j].q0;
+        if (!((lead_mask >> q) & 1) || ntrail[q] >= nlead[q]) return false;
+        cd m[16];
+        if (gate_matrix(g[j], mats, nm, m) != 2) return false;
+        if (ntrail[q] == 0) {
+            for (int e = 0; e < 4; e++) Utrail[q][e] = m[e];
+        } else {
+            cd *U = Utrail[q];
+            cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
+                       m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
+            for (int e = 0; e < 4; e++) U[e] = r[e];
+        }
+        ntrail[q]++;
+        need--;
+        j++;
+    }
+    // trail * lead == I on every basis-changed qubit, letters from U^dag Z U
+    uint64_t xm = 0, zm = 0;
+    int sign = 1;
+    for (int q = 0; q < 64; q++) {
+        const bool inS = (S >> q) & 1;
+        if (nlead[q]) {
+            const cd *A = Utrail[q], *B = Ulead[q];
+            cd P[4] = {A[0] * B[0] + A[1] * B[2], A[0] * B[1] + A[1] * B[3],
+                       A[2] * B[0] + A[3] * B[2], A[2] * B[1] + A[3] * B[3]};
+            if (std::abs(P[0] - 1.0) > 1e-12 || std::abs(P[1]) > 1e-12 || std::abs(P[2]) > 1e-12 ||
+                std::abs(P[3] - 1.0) > 1e-12)
+                return false;
+        }
+        if (!inS) continue;
+        int letter = 3, s = 1;
+        if (nlead[q]) {
+            letter = conj_z(Ulead[q], &s);
+            if (!letter) return false;
+        }
+        sign *= s;
+        if (letter == 1 || letter == 2) xm |= 1ull << q;
+        if (letter == 2 || letter == 3) zm |= 1ull << q;
+    }
+    out.len = j - i;
+    out.xm = xm;
+    out.zm = zm;
+    out.theta = sign * phi / 2;
+    return true;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ config --
@@ -319,7 +467,8 @@ bool validate(int n, const qsim_gate *g, size_t n_gates, const double *mats, siz
 
 // -------------------------------------------------------------------- fusion --
 void fuse(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
-          int fusion, std::vector<FOp> &ops, std::vector<cd> &pool, uint64_t *n_meas) {
+          int fusion, std::vector<FOp> &ops, std::vector<cd> &pool, uint64_t *n_meas,
+          int max_rotation_qubits) {
     ops.clear();
     pool.clear();
     ops.reserve(n_gates / 2 + 16);
@@ -357,6 +506,29 @@ void fuse(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t 
     for (size_t i = 0; i < n_gates; i++) {
         const qsim_gate &x = g[i];
         const int op = x.op;
+        if (fusion == 2 && (op == QSIM_OP_CX || is_basis_gate(x))) {
+            Gadget gd;
+            if (match_gadget(n, g, i, n_gates, mats, n_mats, gd) &&
+                popc(gd.xm | gd.zm) <= max_rotation_qubits) {
+                // gates pending on the rotation's qubits run before it; nothing
+                // after it may be absorbed into an op before it
+                const uint64_t sup = gd.xm | gd.zm;
+                for (int q = 0; q < n; q++)
+                    if ((sup >> q) & 1) {
+                        flush(q);
+                        open2[q] = -1;
+                    }
+                FOp o;
+                o.k = kPauli;
+                o.xm = gd.xm;
+                o.zm = gd.zm;
+                o.mat = pool.size();
+                pool.push_back(cd(std::cos(gd.theta), std::sin(gd.theta)));
+                ops.push_back(o);
+                i += gd.len - 1;
+                continue;
+            }
+        }
         if (is_event(op)) {
             FOp e;
             e.k = 0;
@@ -437,11 +609,13 @@ double merge_cost(int k, qsim_dtype dt) {
     return dt == QSIM_C64 ? 16.0 + alu : 16.0 + 16.0 * alu;
 }
 
+size_t mat_entries(const FOp &o) { return o.pauli() ? 1 : ((size_t)1 << (2 * o.k)); }
+
 void merge_pass(std::vector<FOp> &ops, std::vector<cd> &pool, size_t first, size_t count,
                 int k_max, qsim_dtype dt, std::vector<FOp> &out) {
     if (count == 0) return;
     FOp cur = ops[first];
-    std::vector<cd> curM(pool.begin() + cur.mat, pool.begin() + cur.mat + (1 << (2 * cur.k)));
+    std::vector<cd> curM(pool.begin() + cur.mat, pool.begin() + cur.mat + mat_entries(cur));
     std::vector<cd> E;
     auto flush = [&]() {
         cur.mat = pool.size();
@@ -452,7 +626,9 @@ void merge_pass(std::vector<FOp> &ops, std::vector<cd> &pool, size_t first, size
         const FOp &o = ops[i];
         const uint64_t um = cur.mask() | o.mask();
         const int u = popc(um);
-        if (u <= k_max && merge_cost(u, dt) <= merge_cost(cur.k, dt) + merge_cost(o.k, dt)) {
+        // Pauli rotations are already cheaper than any dense block: never merged
+        if (!cur.pauli() && !o.pauli() && u <= k_max &&
+            merge_cost(u, dt) <= merge_cost(cur.k, dt) + merge_cost(o.k, dt)) {
             uint32_t us[kMaxK];
             int t = 0;
             for (int b = 0; b < 64; b++)
@@ -466,7 +642,7 @@ void merge_pass(std::vector<FOp> &ops, std::vector<cd> &pool, size_t first, size
         } else {
             flush();
             cur = o;
-            curM.assign(pool.begin() + o.mat, pool.begin() + o.mat + (1 << (2 * o.k)));
+            curM.assign(pool.begin() + o.mat, pool.begin() + o.mat + mat_entries(o));
         }
     }
     flush();
@@ -482,9 +658,10 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
     out.gates = n_gates;
     std::vector<FOp> ops;
     std::vector<cd> pool;
-    fuse(n, g, n_gates, mats, n_mats, cfg.fusion, ops, pool, &out.measurements);
-
     const int m = tile_bits_for(cfg, n, dtype);
+    // a rotation must fit one tile together with nothing else
+    fuse(n, g, n_gates, mats, n_mats, cfg.fusion, ops, pool, &out.measurements, m);
+
     out.m = m;
     out.resident = (m == n);
     const int L = forced_low_bits(dtype, m);
@@ -513,6 +690,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
     std::vector<cd> spool;
     spool.reserve(pool.size());
     std::vector<size_t> taken;
+    std::vector<int64_t> skipped_pauli;
 
     while (nxt[HEAD] != HEAD) {
         const int64_t f = nxt[HEAD];
@@ -530,22 +708,44 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             }
             continue;
         }
-        uint64_t T = forced, blocked = 0;
+        // An op may join the pass if its qubits fit the tile and it commutes
+        // with every op skipped so far (disjoint qubits, or two commuting
+        // Pauli rotations), so pulling it ahead of them changes nothing.
+        // The forced low qubits (coalesced tile rows) are dropped for a pass
+        // whose first op would not fit beside them.
+        uint64_t T = popc(forced | ops[f].mask()) <= m ? forced : 0;
+        uint64_t blocked_np = 0, blocked_p = 0;
         size_t skipped = 0;
         taken.clear();
+        skipped_pauli.clear();
         for (int64_t i = f; i != HEAD && skipped < W;) {
             const int64_t ni = nxt[i];
             const FOp &o = ops[i];
             if (o.k == 0) break;  // events bound the scan
             const uint64_t Q = o.mask();
-            if (!(Q & blocked) && popc(T | Q) <= m) {
+            bool ok = popc(T | Q) <= m && !(Q & blocked_np);
+            if (ok && (Q & blocked_p)) {
+                if (!o.pauli()) ok = false;
+                else
+                    for (int64_t s : skipped_pauli)
+                        if (!ops_commute(o, ops[s])) {
+                            ok = false;
+                            break;
+                        }
+            }
+            if (ok) {
                 T |= Q;
                 taken.push_back((size_t)i);
                 unlink(i);
             } else {
-                blocked |= Q;
+                if (o.pauli()) {
+                    blocked_p |= Q;
+                    skipped_pauli.push_back(i);
+                } else {
+                    blocked_np |= Q;
+                }
                 skipped++;
-                if (popc(blocked) >= n) break;
+                if (popc(blocked_np) >= n) break;
             }
             i = ni;
         }
@@ -564,7 +764,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             for (auto &o : merged) {
                 FOp c = o;
                 c.mat = spool.size();
-                spool.insert(spool.end(), pool.begin() + o.mat, pool.begin() + o.mat + (1 << (2 * o.k)));
+                spool.insert(spool.end(), pool.begin() + o.mat, pool.begin() + o.mat + mat_entries(o));
                 sched.push_back(c);
             }
         } else {
@@ -572,12 +772,13 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
                 FOp c = ops[t];
                 c.mat = spool.size();
                 spool.insert(spool.end(), pool.begin() + ops[t].mat,
-                             pool.begin() + ops[t].mat + (1 << (2 * ops[t].k)));
+                             pool.begin() + ops[t].mat + mat_entries(ops[t]));
                 sched.push_back(c);
             }
         }
         p.count = (uint32_t)(sched.size() - p.first);
-        for (size_t i = p.first; i < sched.size(); i++) p.fpa += 8u << sched[i].k;
+        for (size_t i = p.first; i < sched.size(); i++)
+            p.fpa += sched[i].pauli() ? 8u : (8u << sched[i].k);  // a Pauli rotation: 2 complex MACs
         out.passes.push_back(p);
     }
     for (const FOp &o : sched)

@@ -23,18 +23,35 @@ enum : uint8_t { EV_NONE = 0, EV_MEASURE = 1, EV_RESET = 2, EV_BARRIER = 3 };
 // One fused operation.  k > 0: dense 2^k x 2^k matrix at pool[mat], bit j of
 // the local matrix index <-> qubit q[j].  k == 0: an event (measure, reset,
 // barrier) on qubit q[0] (barrier: all qubits).
+//
+// k == kPauli: a Pauli rotation exp(-i theta P) with P = i^{#Y} X^xm Z^zm on the
+// qubits of xm | zm (Y = bit in both); pool[mat] = (cos theta, sin theta).
+constexpr uint8_t kPauli = 7;
+
 struct FOp {
     uint8_t k = 0;
     uint8_t ev = EV_NONE;
     uint16_t flags = 0;
     uint32_t q[kMaxK] = {0, 0, 0, 0, 0, 0};
     uint64_t mat = 0;
+    uint64_t xm = 0, zm = 0;  // Pauli rotations only
+    bool pauli() const { return k == kPauli; }
     uint64_t mask() const {
+        if (k == kPauli) return xm | zm;
         uint64_t m = 0;
         for (int j = 0; j < k; j++) m |= 1ull << q[j];
         return m;
     }
 };
+
+// Two ops may be reordered iff they act on disjoint qubits, or both are Pauli
+// rotations whose Paulis commute (even symplectic product).
+inline bool ops_commute(const FOp &a, const FOp &b) {
+    if (!(a.mask() & b.mask())) return true;
+    if (a.pauli() && b.pauli())
+        return ((__builtin_popcountll(a.xm & b.zm) + __builtin_popcountll(a.zm & b.xm)) & 1) == 0;
+    return false;
+}
 
 // A pass: full-state sweep over tiles of the qubits in `tile` applying ops
 // [first, first+count) in order; or an event pass (tile == 0, count == 1).
@@ -89,9 +106,14 @@ int gate_matrix(const qsim_gate &g, const double *mats, size_t n_mats, cd *out);
 bool validate(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
               std::string &err);
 
-// Stages 1-4 of the paper (fusion=1) or one op per gate (fusion=0).
+// Stages 1-4 of the paper (fusion=1) or one op per gate (fusion=0); fusion=2
+// additionally replaces every recognised Pauli-gadget block (basis change,
+// CX network computing a parity, RZ, the network reversed, the basis change
+// undone) by one Pauli rotation before the four stages run on the rest.
+// Rotations on more than max_rotation_qubits qubits are left as gates.
 void fuse(int n, const qsim_gate *g, size_t n_gates, const double *mats, size_t n_mats,
-          int fusion, std::vector<FOp> &ops, std::vector<cd> &pool, uint64_t *n_meas);
+          int fusion, std::vector<FOp> &ops, std::vector<cd> &pool, uint64_t *n_meas,
+          int max_rotation_qubits);
 
 // Full compile of one stream (fusion + schedule + k-merge) for n qubits.
 void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, size_t n_gates,

@@ -244,14 +244,65 @@ __device__ __forceinline__ void apply_dense_smem(T *tile, int m, const DevOp &op
     }
 }
 
+// Pauli rotation exp(-i theta P), P = i^{ny} X^x Z^z on tile-local masks:
+//   P|j> = ph(j)|j^x>,  ph(j) = i^{ny} (-1)^{popcount(j & z)},
+//   a'_j = cos(theta) a_j - i sin(theta) ph(j^x) a_{j^x}.
+// With x = 0 it is diagonal: a'_j = (cos - i sin (-1)^{popcount(j&z)}) a_j.
 template <typename T, int NT>
+__device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, const T *mats) {
+    const unsigned x = op.lq[0] | ((unsigned)op.lq[1] << 8);
+    const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
+    const T cs = mats[op.mat];
+    const auto c = cs.x, s = cs.y;
+    const unsigned Nt = 1u << m;
+    if (x == 0) {
+        for (unsigned j = threadIdx.x; j < Nt; j += NT) {
+            const auto sg = (__popc(j & z) & 1) ? -s : s;
+            const T a = tile[j];
+            T r;
+            r.x = c * a.x + sg * a.y;  // (c - i sg)(ax + i ay)
+            r.y = c * a.y - sg * a.x;
+            tile[j] = r;
+        }
+        return;
+    }
+    // -i * i^{ny} = i^{(ny + 3) mod 4}: multiply by one of 1, i, -1, -i
+    const int e = (__popc(x & z) + 3) & 3;
+    const int low = __ffs(x) - 1;
+    for (unsigned g = threadIdx.x; g < Nt / 2; g += NT) {
+        const unsigned j = ins0(g, low), k = j ^ x;
+        const T aj = tile[j], ak = tile[k];
+        const auto sj = (__popc(j & z) & 1) ? -s : s;  // sin * (-1)^{popcount(j&z)}
+        const auto sk = (__popc(k & z) & 1) ? -s : s;
+        // rotation of a complex number by i^e
+        auto rot = [e](T v) {
+            T r;
+            if (e == 0) { r.x = v.x; r.y = v.y; }
+            else if (e == 1) { r.x = -v.y; r.y = v.x; }
+            else if (e == 2) { r.x = -v.x; r.y = -v.y; }
+            else { r.x = v.y; r.y = -v.x; }
+            return r;
+        };
+        const T rk = rot(ak), rj = rot(aj);
+        T nj, nk;
+        nj.x = c * aj.x + sk * rk.x;
+        nj.y = c * aj.y + sk * rk.y;
+        nk.x = c * ak.x + sj * rj.x;
+        nk.y = c * ak.y + sj * rj.y;
+        tile[j] = nj;
+        tile[k] = nk;
+    }
+}
+
+template <typename T, int NT, int KMAX>
 __device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const T *mats, T *mbuf) {
     switch (op.k) {
+        case 7: apply_pauli<T, NT>(tile, m, op, mats); break;
         case 1: apply_dense_reg<1, T, NT>(tile, m, op, mats); break;
         case 2: apply_dense_reg<2, T, NT>(tile, m, op, mats); break;
-        case 3: apply_dense_smem<3, T, NT>(tile, m, op, mats, mbuf); break;
-        case 4: apply_dense_smem<4, T, NT>(tile, m, op, mats, mbuf); break;
-        case 5: apply_dense_smem<5, T, NT>(tile, m, op, mats, mbuf); break;
+        case 3: if constexpr (KMAX >= 3) apply_dense_smem<3, T, NT>(tile, m, op, mats, mbuf); break;
+        case 4: if constexpr (KMAX >= 4) apply_dense_smem<4, T, NT>(tile, m, op, mats, mbuf); break;
+        case 5: if constexpr (KMAX >= 5) apply_dense_smem<5, T, NT>(tile, m, op, mats, mbuf); break;
         default: break;
     }
 }
@@ -278,7 +329,7 @@ struct TileArgs {
 
 constexpr int kMaxHi = 1024;  // 2^(m - L) entries, m - L <= 10
 
-template <typename R, int NT>
+template <typename R, int NT, int KMAX>
 __global__ void __launch_bounds__(NT) k_tile_pass(TileArgs a) {
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -310,15 +361,36 @@ __global__ void __launch_bounds__(NT) k_tile_pass(TileArgs a) {
     __syncthreads();
     T *st = reinterpret_cast<T *>(a.state);
     const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
-    for (unsigned l = threadIdx.x; l < Nt; l += NT) tile[l] = st[hi_off[l >> L] | (l & Lmask)];
+    if (L >= 1) {
+        // pairs (2p, 2p+1) are adjacent in global memory: one 16/32-byte access each
+        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
+            const unsigned l = 2 * p;
+            const uint64_t gi = hi_off[l >> L] | (l & Lmask);
+            const T v0 = st[gi], v1 = st[gi + 1];
+            tile[l] = v0;
+            tile[l + 1] = v1;
+        }
+    } else {
+        for (unsigned l = threadIdx.x; l < Nt; l += NT) tile[l] = st[hi_off[l >> L] | (l & Lmask)];
+    }
     __syncthreads();
     const T *mats = reinterpret_cast<const T *>(a.mats);
     for (uint32_t i = 0; i < a.n_ops; i++) {
         const DevOp op = load_op(a.ops + i);
-        apply_op<T, NT>(tile, a.m, op, mats, mbuf);
+        apply_op<T, NT, KMAX>(tile, a.m, op, mats, mbuf);
         __syncthreads();
     }
-    for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];
+    __syncthreads();
+    if (L >= 1) {
+        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
+            const unsigned l = 2 * p;
+            const uint64_t gi = hi_off[l >> L] | (l & Lmask);
+            st[gi] = tile[l];
+            st[gi + 1] = tile[l + 1];
+        }
+    } else {
+        for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];
+    }
 }
 
 // -------------------------------------------------------------- resident --
@@ -338,7 +410,7 @@ __device__ void run_resident(const Instance &in, T *tile, double *red, int *bcas
     for (uint64_t i = 0; i < in.n_ops; i++) {
         const DevOp op = load_op(in.ops + i);
         if (op.k) {
-            apply_op<T, NT>(tile, n, op, mats, mbuf);
+            apply_op<T, NT, 5>(tile, n, op, mats, mbuf);
             __syncthreads();
             continue;
         }
@@ -568,10 +640,12 @@ cudaError_t setup_kernels() {
 #define QSIM_ATTR(fn)                                                                      \
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big - 24 * 1024); \
     if (e != cudaSuccess) return e;
-    QSIM_ATTR((k_tile_pass<float, 256>));
-    QSIM_ATTR((k_tile_pass<double, 256>));
-    QSIM_ATTR((k_tile_pass<float, 512>));
-    QSIM_ATTR((k_tile_pass<double, 512>));
+    QSIM_ATTR((k_tile_pass<float, 256, 2>));
+    QSIM_ATTR((k_tile_pass<double, 256, 2>));
+    QSIM_ATTR((k_tile_pass<float, 512, 2>));
+    QSIM_ATTR((k_tile_pass<double, 512, 2>));
+    QSIM_ATTR((k_tile_pass<float, 256, 5>));
+    QSIM_ATTR((k_tile_pass<double, 256, 5>));
     QSIM_ATTR((k_resident_one<float, 256>));
     QSIM_ATTR((k_resident_one<double, 256>));
     QSIM_ATTR((k_resident_batch<float, 256>));
@@ -580,8 +654,8 @@ cudaError_t setup_kernels() {
     return cudaSuccess;
 }
 
-cudaError_t launch_tile_pass(int dtype, int threads, void *state, int n, int m, uint64_t tile_mask,
-                             const DevOp *ops, uint32_t n_ops, const void *mats,
+cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
+                             uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
                              const MeasCtl *ctl, cudaStream_t s) {
     TileArgs a;
     a.state = state;
@@ -592,16 +666,24 @@ cudaError_t launch_tile_pass(int dtype, int threads, void *state, int n, int m, 
     a.n_ops = n_ops;
     a.n = n;
     a.m = m;
-    a.L = dtype == 0 ? (m < 4 ? m : 4) : (m < 3 ? m : 3);
+    // contiguous low qubits of the tile (the coalesced run length), capped at
+    // 128-byte runs; a pass may lack them when its first op needs the room
+    int low = __builtin_ctzll(~tile_mask);
+    const int cap = dtype == 0 ? 4 : 3;
+    a.L = low < cap ? low : cap;
+    if (a.L > m) a.L = m;
     const unsigned grid = 1u << (n - m);
     const size_t es = dtype == 0 ? 8 : 16;
-    const size_t smem = (es << m) + es * 32 * 32;
-    if (dtype == 0) {
-        if (threads == 512) k_tile_pass<float, 512><<<grid, 512, smem, s>>>(a);
-        else k_tile_pass<float, 256><<<grid, 256, smem, s>>>(a);
+    const size_t smem = (es << m) + (kmax > 2 ? es * 32 * 32 : 0);  // + staging of a k >= 3 matrix
+    if (kmax > 2) {
+        if (dtype == 0) k_tile_pass<float, 256, 5><<<grid, 256, smem, s>>>(a);
+        else k_tile_pass<double, 256, 5><<<grid, 256, smem, s>>>(a);
+    } else if (dtype == 0) {
+        if (threads == 512) k_tile_pass<float, 512, 2><<<grid, 512, smem, s>>>(a);
+        else k_tile_pass<float, 256, 2><<<grid, 256, smem, s>>>(a);
     } else {
-        if (threads == 512) k_tile_pass<double, 512><<<grid, 512, smem, s>>>(a);
-        else k_tile_pass<double, 256><<<grid, 256, smem, s>>>(a);
+        if (threads == 512) k_tile_pass<double, 512, 2><<<grid, 512, smem, s>>>(a);
+        else k_tile_pass<double, 256, 2><<<grid, 256, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

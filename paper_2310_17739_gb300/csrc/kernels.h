@@ -75,8 +75,10 @@ cudaError_t setup_kernels();
 size_t resident_smem_bytes(int dtype, int n);
 int max_resident_bits(int dtype);
 
-cudaError_t launch_tile_pass(int dtype, int threads, void *state, int n, int m, uint64_t tile_mask,
-                             const DevOp *ops, uint32_t n_ops, const void *mats,
+// kmax: largest op size (qubits) in the launched ops; <= 2 selects the
+// register-lean instantiation without the k >= 3 paths.
+cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
+                             uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
                              const MeasCtl *ctl, cudaStream_t s);
 cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s);
 cudaError_t launch_resident_batch(int dtype, int threads, const Instance *d_insts, int count,

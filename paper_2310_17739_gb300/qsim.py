@@ -26,6 +26,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 C64, C128 = 0, 1
+PAULI_K = 7  # op-size marker of a Pauli rotation in the compiled op list
 OK, E_INVAL, E_OOM, E_CUDA, E_ZEROPROB, E_TIMEOUT, E_STATE = range(7)
 MEAS_ASSERT = 1
 _vp, _sz, _u64, _i32, _dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
@@ -342,6 +343,11 @@ def fuse(n, gates, mats=None, dtype=C64, **cfg):
         k = int(ok[i])
         if k == 0:
             out.append(("event", int(oq[6 * i + 1]), int(oq[6 * i]), int(oq[6 * i + 2])))
+        elif k == PAULI_K:
+            xm = int(oq[6 * i]) | (int(oq[6 * i + 1]) << 32)
+            zm = int(oq[6 * i + 2]) | (int(oq[6 * i + 3]) << 32)
+            off = int(om[i])
+            out.append(("pauli", xm, zm, float(np.arctan2(md[off + 1], md[off]))))
         else:
             d = 1 << k
             off = int(om[i])

@@ -89,7 +89,7 @@ def test_generic_matrices_non_unitary(dtype):
     assert np.abs(got - ref).max() <= tol * scale
 
 
-@pytest.mark.parametrize("fusion,k_max", [(0, 2), (1, 2), (1, 3), (1, 4), (1, 5)])
+@pytest.mark.parametrize("fusion,k_max", [(0, 2), (1, 2), (1, 3), (1, 4), (1, 5), (2, 2), (2, 4)])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_fusion_levels(dtype, fusion, k_max):
     n = 15
@@ -230,3 +230,18 @@ def test_empty_and_edge_inputs():
     sim2 = qs.Sim(2, "c64")
     with pytest.raises(qs.QsimError):
         sim2.set_config(tile_bits=20)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,tile_bits", [(9, 0), (16, 10), (16, 13), (21, 13)])
+def test_pauli_rotations_with_measurements(dtype, n, tile_bits):
+    """Gadget recognition (fusion=2) with mid-circuit measurements, resident and tiled."""
+    gates = 3000 if n < 21 else 1500
+    c = W.ucc_circuit(n, seed=40 + n, n_gadgets=None, w_lo=2, w_hi=8 if n > 9 else 6,
+                      theta="normal0.1", target_gates=gates, n_meas=6)
+    ref, r = run_oracle(c, seed=11)
+    sim, st = run_gpu(c, dtype, seed=11, config=dict(fusion=2, tile_bits=tile_bits))
+    assert st == 0
+    out, prob = sim.outcomes()
+    check_outcomes(dtype, out, prob, r, 11)
+    check_state(dtype, sim.state(), ref)

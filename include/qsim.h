@@ -163,7 +163,10 @@ typedef void (*qsim_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 QSIM_API qsim_status qsim_create(int n_qubits, qsim_dtype dtype, void *stream,
                         qsim_alloc_fn alloc, qsim_free_fn free_fn, void *user,
                         qsim_ctx **out);
-/* Releases the state and every buffer of the context (stream-ordered). */
+/* Releases the state and every buffer of the context (stream-ordered),
+ * including the device memory of programs compiled on it that are still
+ * alive; those programs can no longer be run but must still be passed to
+ * qsim_program_free (which then only releases their host memory). */
 QSIM_API qsim_status qsim_destroy(qsim_ctx *ctx);
 QSIM_API qsim_status qsim_set_stream(qsim_ctx *ctx, void *stream);
 QSIM_API qsim_status qsim_set_config(qsim_ctx *ctx, const qsim_config *cfg);

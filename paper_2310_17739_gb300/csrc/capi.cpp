@@ -153,6 +153,8 @@ struct qsim_ctx {
     size_t prof_used = 0;
     double prof_flops = 0, prof_bytes = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    // live programs compiled on this context (released and orphaned by qsim_destroy)
+    std::vector<qsim_program *> programs;
 };
 
 struct qsim_program {
@@ -544,6 +546,12 @@ qsim_status qsim_create(int n, qsim_dtype dtype, void *stream, qsim_alloc_fn all
 qsim_status qsim_destroy(qsim_ctx *c) {
     if (!c) return QSIM_OK;
     cudaSetDevice(c->device);
+    // programs still alive release their device buffers now and become orphans
+    for (qsim_program *p : c->programs) {
+        for (auto &dc : p->chunks) release_chunk(c, dc);
+        p->owner = nullptr;
+    }
+    c->programs.clear();
     dfree(c, c->state, c->state_bytes);
     dfree(c, c->ctl, sizeof(MeasCtl));
     dfree(c, c->log, c->log_cap * sizeof(MeasRec));
@@ -650,6 +658,7 @@ qsim_status qsim_compile(qsim_ctx *c, const qsim_gate *g, size_t ng, const doubl
         qsim_program_free(prog.release());
         return s;
     }
+    c->programs.push_back(prog.get());
     *out = prog.release();
     return QSIM_OK;
 }
@@ -673,9 +682,11 @@ qsim_status qsim_program_get_info(const qsim_program *p, qsim_program_info *info
 
 qsim_status qsim_program_free(qsim_program *p) {
     if (!p) return QSIM_OK;
-    if (p->owner) {
-        cudaSetDevice(p->owner->device);
-        for (auto &dc : p->chunks) release_chunk(p->owner, dc);
+    if (p->owner) {  // an orphan (its context destroyed) holds no device memory any more
+        qsim_ctx *c = p->owner;
+        cudaSetDevice(c->device);
+        for (auto &dc : p->chunks) release_chunk(c, dc);
+        c->programs.erase(std::remove(c->programs.begin(), c->programs.end(), p), c->programs.end());
     }
     delete p;
     return QSIM_OK;

@@ -307,6 +307,20 @@ __device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const 
     }
 }
 
+// Asynchronous global -> shared copies (cp.async): issued without waiting,
+// completed by cp_async_wait_all (commit + wait for all of this thread's groups).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ DevOp load_op(const DevOp *p) {
     uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
     DevOp o;
@@ -361,18 +375,20 @@ __global__ void __launch_bounds__(NT) k_tile_pass(TileArgs a) {
     __syncthreads();
     T *st = reinterpret_cast<T *>(a.state);
     const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
-    if (L >= 1) {
-        // pairs (2p, 2p+1) are adjacent in global memory: one 16/32-byte access each
-        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
-            const unsigned l = 2 * p;
-            const uint64_t gi = hi_off[l >> L] | (l & Lmask);
-            const T v0 = st[gi], v1 = st[gi + 1];
-            tile[l] = v0;
-            tile[l + 1] = v1;
+    // 16-byte chunks (two c64 / one c128 amplitude) are contiguous in global
+    // memory whenever the tile holds qubit 0 (L >= 1) or the amplitude is 16 B.
+    constexpr unsigned per = 16 / sizeof(T);
+    const bool vec = sizeof(T) == 16 || L >= 1;
+    // gather with asynchronous copies: every copy of the tile is in flight at once
+    if (vec) {
+        for (unsigned p = threadIdx.x; p < Nt / per; p += NT) {
+            const unsigned l = p * per;
+            cp_async16(tile + l, st + (hi_off[l >> L] | (l & Lmask)));
         }
     } else {
-        for (unsigned l = threadIdx.x; l < Nt; l += NT) tile[l] = st[hi_off[l >> L] | (l & Lmask)];
+        for (unsigned l = threadIdx.x; l < Nt; l += NT) cp_async8(tile + l, st + (hi_off[l >> L] | (l & Lmask)));
     }
+    cp_async_wait_all();
     __syncthreads();
     const T *mats = reinterpret_cast<const T *>(a.mats);
     for (uint32_t i = 0; i < a.n_ops; i++) {
@@ -381,12 +397,11 @@ __global__ void __launch_bounds__(NT) k_tile_pass(TileArgs a) {
         __syncthreads();
     }
     __syncthreads();
-    if (L >= 1) {
-        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
-            const unsigned l = 2 * p;
-            const uint64_t gi = hi_off[l >> L] | (l & Lmask);
-            st[gi] = tile[l];
-            st[gi + 1] = tile[l + 1];
+    if (vec) {
+        for (unsigned p = threadIdx.x; p < Nt / per; p += NT) {
+            const unsigned l = p * per;
+            *reinterpret_cast<uint4 *>(st + (hi_off[l >> L] | (l & Lmask))) =
+                *reinterpret_cast<const uint4 *>(tile + l);
         }
     } else {
         for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];

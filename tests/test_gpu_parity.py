@@ -245,3 +245,27 @@ def test_pauli_rotations_with_measurements(dtype, n, tile_bits):
     out, prob = sim.outcomes()
     check_outcomes(dtype, out, prob, r, 11)
     check_state(dtype, sim.state(), ref)
+
+
+def test_program_outlives_its_context():
+    """Destroying a context releases its programs' device memory; freeing such an
+    orphaned program afterwards (in any order) is safe and running it is refused."""
+    c = W.ucc_circuit(12, seed=1, n_gadgets=10, w_lo=2, w_hi=4, target_gates=500)
+    sims, progs = [], []
+    for fusion in (1, 2):
+        s = qs.Sim(12, "c64", config=dict(fusion=fusion, tile_bits=9))
+        progs.append(s.compile(c.gates))
+        sims.append(s)
+    sims[0].close()
+    progs[0].free()                    # orphan freed after its context
+    progs[1].free()                    # normal order
+    sims[1].close()
+    s = qs.Sim(12, "c64")
+    p = s.compile(c.gates)
+    other = qs.Sim(12, "c64")
+    with pytest.raises(qs.QsimError):
+        other.run(p)                   # a program runs only on its own context
+    s.close()
+    with pytest.raises(qs.QsimError):
+        other.run(p)
+    del p

@@ -344,7 +344,9 @@ qsim_status launch_measure(qsim_ctx *c, int q, int mode, int reset, uint64_t see
 }
 
 qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
-    const int threads = c->cfg.threads == 512 ? 512 : 256;
+    // 512 threads per tile for complex64 (more warps in flight per SM); the
+    // complex128 tile kernel keeps 256 (its 512-thread build spills)
+    const int threads = c->cfg.threads ? c->cfg.threads : (c->dtype == QSIM_C64 ? 512 : 256);
     if (dc.resident) {
         qsim_status s = ensure_log(c, c->log_n + dc.measurements);
         if (s != QSIM_OK) return s;

@@ -191,20 +191,33 @@ __device__ __forceinline__ void apply_dense_reg(T *tile, int m, const DevOp &op,
     T mr[D * D];
 #pragma unroll
     for (int i = 0; i < D * D; i++) mr[i] = M[i];
+    // U groups per thread per iteration, loaded before any is stored (groups
+    // are disjoint), so shared-memory latency overlaps across them
+    constexpr int U = K == 1 ? 4 : 2;
     const unsigned G = 1u << (m - K);
-    for (unsigned g = threadIdx.x; g < G; g += NT) {
-        unsigned b = g;
+    for (unsigned g0 = threadIdx.x; g0 < G; g0 += U * NT) {
+        unsigned bb[U];
+        T x[U][D];
 #pragma unroll
-        for (int j = 0; j < K; j++) b = ins0(b, sp[j]);
-        T x[D];
+        for (int u = 0; u < U; u++) {
+            const unsigned g = g0 + u * NT;
+            unsigned b = g < G ? g : 0;
 #pragma unroll
-        for (int l = 0; l < D; l++) x[l] = tile[b + off[l]];
+            for (int j = 0; j < K; j++) b = ins0(b, sp[j]);
+            bb[u] = b;
 #pragma unroll
-        for (int r = 0; r < D; r++) {
-            T acc = czero(x[0]);
+            for (int l = 0; l < D; l++) x[u][l] = tile[b + off[l]];
+        }
 #pragma unroll
-            for (int c = 0; c < D; c++) cmac(acc, mr[r * D + c], x[c]);
-            tile[b + off[r]] = acc;
+        for (int u = 0; u < U; u++) {
+            if (g0 + u * NT >= G) break;
+#pragma unroll
+            for (int r = 0; r < D; r++) {
+                T acc = czero(x[u][0]);
+#pragma unroll
+                for (int c = 0; c < D; c++) cmac(acc, mr[r * D + c], x[u][c]);
+                tile[bb[u] + off[r]] = acc;
+            }
         }
     }
 }
@@ -269,28 +282,44 @@ __device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, con
     // -i * i^{ny} = i^{(ny + 3) mod 4}: multiply by one of 1, i, -1, -i
     const int e = (__popc(x & z) + 3) & 3;
     const int low = __ffs(x) - 1;
-    for (unsigned g = threadIdx.x; g < Nt / 2; g += NT) {
-        const unsigned j = ins0(g, low), k = j ^ x;
-        const T aj = tile[j], ak = tile[k];
-        const auto sj = (__popc(j & z) & 1) ? -s : s;  // sin * (-1)^{popcount(j&z)}
-        const auto sk = (__popc(k & z) & 1) ? -s : s;
-        // rotation of a complex number by i^e
-        auto rot = [e](T v) {
-            T r;
-            if (e == 0) { r.x = v.x; r.y = v.y; }
-            else if (e == 1) { r.x = -v.y; r.y = v.x; }
-            else if (e == 2) { r.x = -v.x; r.y = -v.y; }
-            else { r.x = v.y; r.y = -v.x; }
-            return r;
-        };
-        const T rk = rot(ak), rj = rot(aj);
-        T nj, nk;
-        nj.x = c * aj.x + sk * rk.x;
-        nj.y = c * aj.y + sk * rk.y;
-        nk.x = c * ak.x + sj * rj.x;
-        nk.y = c * ak.y + sj * rj.y;
-        tile[j] = nj;
-        tile[k] = nk;
+    // rotation of a complex number by i^e
+    auto rot = [e](T v) {
+        T r;
+        if (e == 0) { r.x = v.x; r.y = v.y; }
+        else if (e == 1) { r.x = -v.y; r.y = v.x; }
+        else if (e == 2) { r.x = -v.x; r.y = -v.y; }
+        else { r.x = v.y; r.y = -v.x; }
+        return r;
+    };
+    // U pairs per thread per iteration, all loaded before any is stored (the
+    // pairs are disjoint), so shared-memory latency overlaps across them
+    constexpr int U = 4;
+    const unsigned P = Nt / 2;
+    for (unsigned g0 = threadIdx.x; g0 < P; g0 += U * NT) {
+        unsigned jj[U];
+        T aj[U], ak[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned g = g0 + u * NT;
+            jj[u] = ins0(g < P ? g : 0, low);
+            aj[u] = tile[jj[u]];
+            ak[u] = tile[jj[u] ^ x];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (g0 + u * NT >= P) break;
+            const unsigned j = jj[u], k = j ^ x;
+            const auto sj = (__popc(j & z) & 1) ? -s : s;  // sin * (-1)^{popcount(j&z)}
+            const auto sk = (__popc(k & z) & 1) ? -s : s;
+            const T rk = rot(ak[u]), rj = rot(aj[u]);
+            T nj, nk;
+            nj.x = c * aj[u].x + sk * rk.x;
+            nj.y = c * aj[u].y + sk * rk.y;
+            nk.x = c * ak[u].x + sj * rj.x;
+            nk.y = c * ak[u].y + sj * rj.y;
+            tile[j] = nj;
+            tile[k] = nk;
+        }
     }
 }
 
@@ -344,7 +373,7 @@ struct TileArgs {
 constexpr int kMaxHi = 1024;  // 2^(m - L) entries, m - L <= 10
 
 template <typename R, int NT, int KMAX>
-__global__ void __launch_bounds__(NT) k_tile_pass(TileArgs a) {
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a) {
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);

@@ -17,6 +17,9 @@
 #include "compiler.h"
 #include "kernels.h"
 
+static_assert(qsim::kTilePassOps == qsim::kPassOps && qsim::kTilePassMats == qsim::kPassMats,
+              "the compiler's per-pass limits must match the tile kernel's shared-memory slices");
+
 using qsim::cd;
 using qsim::Config;
 using qsim::DevOp;
@@ -105,7 +108,9 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
             } else {
                 for (int j = 0; j < o.k; j++) d.lq[j] = (uint8_t)local(o.q[j]);
             }
-            d.mat = (uint32_t)o.mat;
+            // the tile kernel indexes the pass's own coefficient slice; the
+            // resident kernel walks the whole pool
+            d.mat = (uint32_t)(hp.resident ? o.mat : o.mat - p.mat_first);
             fused++;
         }
     }
@@ -380,7 +385,8 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
                             c->prof_used < c->prof_ev.size();
         if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
         CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile,
-                                  dc.d_ops + p.first, p.count, dc.d_mats, c->ctl, c->stream),
+                                  dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
+                                  p.mat_count, c->ctl, c->stream),
            "tile pass launch");
         if (sample) {
             CK(cudaEventRecord(c->prof_ev[c->prof_used].second, c->stream), "profile event");

@@ -715,13 +715,17 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
         // whose first op would not fit beside them.
         uint64_t T = popc(forced | ops[f].mask()) <= m ? forced : 0;
         uint64_t blocked_np = 0, blocked_p = 0;
-        size_t skipped = 0;
+        size_t skipped = 0, n_mats = 0;
         taken.clear();
         skipped_pauli.clear();
         for (int64_t i = f; i != HEAD && skipped < W;) {
             const int64_t ni = nxt[i];
             const FOp &o = ops[i];
             if (o.k == 0) break;  // events bound the scan
+            // the tile kernel holds a pass's ops and coefficients in shared memory
+            if (taken.size() >= (size_t)kTilePassOps ||
+                n_mats + mat_entries(o) > (size_t)kTilePassMats)
+                break;
             const uint64_t Q = o.mask();
             bool ok = popc(T | Q) <= m && !(Q & blocked_np);
             if (ok && (Q & blocked_p)) {
@@ -736,6 +740,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             if (ok) {
                 T |= Q;
                 taken.push_back((size_t)i);
+                n_mats += mat_entries(o);
                 unlink(i);
             } else {
                 if (o.pauli()) {
@@ -751,35 +756,47 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
         }
         // Pad the tile to exactly m qubits (lowest unused first).
         for (int b = 0; b < n && popc(T) < m; b++) T |= 1ull << b;
-        Pass p;
-        p.tile = T;
-        p.first = sched.size();
+        std::vector<FOp> body;
+        body.reserve(taken.size());
         if (cfg.k_max > 2) {
             // merge in the pass's order into <= k_max-qubit dense blocks
             std::vector<FOp> tmp;
             tmp.reserve(taken.size());
             for (size_t t : taken) tmp.push_back(ops[t]);
-            std::vector<FOp> merged;
-            merge_pass(tmp, pool, 0, tmp.size(), k_max, dtype, merged);
-            for (auto &o : merged) {
-                FOp c = o;
-                c.mat = spool.size();
-                spool.insert(spool.end(), pool.begin() + o.mat, pool.begin() + o.mat + mat_entries(o));
-                sched.push_back(c);
-            }
+            merge_pass(tmp, pool, 0, tmp.size(), k_max, dtype, body);
         } else {
-            for (size_t t : taken) {
-                FOp c = ops[t];
-                c.mat = spool.size();
-                spool.insert(spool.end(), pool.begin() + ops[t].mat,
-                             pool.begin() + ops[t].mat + mat_entries(ops[t]));
-                sched.push_back(c);
-            }
+            for (size_t t : taken) body.push_back(ops[t]);
         }
-        p.count = (uint32_t)(sched.size() - p.first);
-        for (size_t i = p.first; i < sched.size(); i++)
-            p.fpa += sched[i].pauli() ? 8u : (8u << sched[i].k);  // a Pauli rotation: 2 complex MACs
-        out.passes.push_back(p);
+        // Emit as one pass, or as several consecutive passes over the same
+        // tile when merged blocks exceed the per-pass coefficient budget.
+        Pass p;
+        auto open_pass = [&]() {
+            p = Pass();
+            p.tile = T;
+            p.first = sched.size();
+            p.mat_first = spool.size();
+        };
+        auto close_pass = [&]() {
+            p.count = (uint32_t)(sched.size() - p.first);
+            p.mat_count = (uint32_t)(spool.size() - p.mat_first);
+            for (size_t i = p.first; i < sched.size(); i++)
+                p.fpa += sched[i].pauli() ? 8u : (8u << sched[i].k);  // a Pauli rotation: 2 complex MACs
+            if (p.count) out.passes.push_back(p);
+        };
+        open_pass();
+        for (const FOp &o : body) {
+            const size_t e = mat_entries(o);
+            if (sched.size() - p.first >= (size_t)kTilePassOps ||
+                spool.size() - p.mat_first + e > (size_t)kTilePassMats) {
+                close_pass();
+                open_pass();
+            }
+            FOp c = o;
+            c.mat = spool.size();
+            spool.insert(spool.end(), pool.begin() + o.mat, pool.begin() + o.mat + e);
+            sched.push_back(c);
+        }
+        close_pass();
     }
     for (const FOp &o : sched)
         if (o.k) out.hist[o.k]++;

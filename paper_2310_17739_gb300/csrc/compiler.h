@@ -64,7 +64,14 @@ struct Pass {
     uint16_t flags = 0;   // event flags (bit 0: assertion mode)
     uint32_t q = 0;       // event qubit
     uint32_t fpa = 0;     // algorithmic real flops per amplitude of the pass (8 * 2^k per op)
+    uint64_t mat_first = 0;  // the pass's coefficients: pool[mat_first, mat_first + mat_count)
+    uint32_t mat_count = 0;
 };
+
+// Per-pass limits of the tile kernel (its ops and coefficients are copied
+// into shared memory next to the tile): ops, and complex coefficient values.
+constexpr int kTilePassOps = 256;
+constexpr int kTilePassMats = 1024;
 
 struct Config {
     int fusion = 1;

@@ -222,15 +222,20 @@ __device__ __forceinline__ void apply_dense_reg(T *tile, int m, const DevOp &op,
     }
 }
 
-// K >= 3: the matrix is staged in shared memory (mbuf, broadcast reads), so
-// that its 4^K entries are not all held in registers.
-template <int K, typename T, int NT>
+// K >= 3: the matrix is read from shared memory (broadcast reads), so that its
+// 4^K entries are not all held in registers.  STAGE: copy it from global into
+// mbuf first; otherwise `mats` already points into shared memory.
+template <int K, typename T, int NT, bool STAGE>
 __device__ __forceinline__ void apply_dense_smem(T *tile, int m, const DevOp &op, const T *mats,
                                                  T *mbuf) {
     constexpr int D = 1 << K;
     const T *M = mats + op.mat;
-    for (int i = threadIdx.x; i < D * D; i += NT) mbuf[i] = M[i];
-    __syncthreads();
+    if constexpr (STAGE) {
+        for (int i = threadIdx.x; i < D * D; i += NT) mbuf[i] = M[i];
+        __syncthreads();
+    } else {
+        mbuf = const_cast<T *>(M);
+    }
     int sp[K];
     unsigned off[D];
     group_layout<K>(op, sp, off);
@@ -323,15 +328,17 @@ __device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, con
     }
 }
 
-template <typename T, int NT, int KMAX>
+// STAGE: matrices come from global memory (k >= 3 ones are staged in mbuf);
+// otherwise `mats` is the pass's coefficient slice already in shared memory.
+template <typename T, int NT, int KMAX, bool STAGE = true>
 __device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const T *mats, T *mbuf) {
     switch (op.k) {
         case 7: apply_pauli<T, NT>(tile, m, op, mats); break;
         case 1: apply_dense_reg<1, T, NT>(tile, m, op, mats); break;
         case 2: apply_dense_reg<2, T, NT>(tile, m, op, mats); break;
-        case 3: if constexpr (KMAX >= 3) apply_dense_smem<3, T, NT>(tile, m, op, mats, mbuf); break;
-        case 4: if constexpr (KMAX >= 4) apply_dense_smem<4, T, NT>(tile, m, op, mats, mbuf); break;
-        case 5: if constexpr (KMAX >= 5) apply_dense_smem<5, T, NT>(tile, m, op, mats, mbuf); break;
+        case 3: if constexpr (KMAX >= 3) apply_dense_smem<3, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
+        case 4: if constexpr (KMAX >= 4) apply_dense_smem<4, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
+        case 5: if constexpr (KMAX >= 5) apply_dense_smem<5, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
         default: break;
     }
 }
@@ -358,16 +365,22 @@ __device__ __forceinline__ DevOp load_op(const DevOp *p) {
 }
 
 // ------------------------------------------------------------ tile pass --
+// One pass: its op slice ops[0, n_ops) and coefficient slice (mat_count
+// complex values starting at element mat_first of the pool; op.mat is relative
+// to mat_first) are copied into shared memory together with the tile.
 struct TileArgs {
     void *state;
     const DevOp *ops;
     const void *mats;
     const MeasCtl *ctl;
-    uint64_t tile_mask;
     uint32_t n_ops;
+    uint32_t mat_first;
+    uint32_t mat_count;
     int n;
     int m;
     int L;
+    uint8_t tq[16];   // tile qubits, ascending (m entries)
+    uint8_t ntq[48];  // other qubits, ascending (n - m entries)
 };
 
 constexpr int kMaxHi = 1024;  // 2^(m - L) entries, m - L <= 10
@@ -377,38 +390,40 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
-    T *mbuf = tile + (1u << a.m);  // staging of one k >= 3 matrix (<= 32 x 32)
+    T *mats_s = tile + (1u << a.m);                                   // kPassMats values
+    DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);     // kPassOps ops
     __shared__ uint64_t hi_off[kMaxHi];
-    __shared__ int tq[64];
-    __shared__ int ntq[64];
-    if (a.ctl->status) return;
-    if (threadIdx.x == 0) {
-        int t = 0, u = 0;
-        for (int b = 0; b < a.n; b++) {
-            if ((a.tile_mask >> b) & 1ull) tq[t++] = b;
-            else ntq[u++] = b;
+    const int status = a.ctl->status;  // checked once everything is in flight
+    // 1. the pass's ops and coefficients: asynchronous copies
+    for (unsigned i = threadIdx.x; i < a.n_ops; i += NT) cp_async16(ops_s + i, a.ops + i);
+    {
+        const T *gm = reinterpret_cast<const T *>(a.mats) + a.mat_first;
+        for (unsigned i = threadIdx.x; i < a.mat_count; i += NT) {
+            if constexpr (sizeof(T) == 16) cp_async16(mats_s + i, gm + i);
+            else cp_async8(mats_s + i, gm + i);
         }
     }
-    __syncthreads();
+    // 2. global offsets of the tile rows: non-tile bits from blockIdx, tile bits
+    //    above the L contiguous low ones from the row index
     uint64_t base = 0;
     {
         const uint64_t bid = blockIdx.x;
-        for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << ntq[j];
+        for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << a.ntq[j];
     }
     const int L = a.L, hib = a.m - L;
     for (int r = threadIdx.x; r < (1 << hib); r += NT) {
         uint64_t o = base;
-        for (int j = 0; j < hib; j++) o |= ((uint64_t)((r >> j) & 1)) << tq[L + j];
+        for (int j = 0; j < hib; j++) o |= ((uint64_t)((r >> j) & 1)) << a.tq[L + j];
         hi_off[r] = o;
     }
     __syncthreads();
     T *st = reinterpret_cast<T *>(a.state);
     const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
-    // 16-byte chunks (two c64 / one c128 amplitude) are contiguous in global
-    // memory whenever the tile holds qubit 0 (L >= 1) or the amplitude is 16 B.
+    // 3. gather: 16-byte chunks (two c64 / one c128 amplitude) are contiguous in
+    //    global memory whenever the tile holds qubit 0 (L >= 1) or amplitudes
+    //    are 16 B; every copy of the tile is in flight at once
     constexpr unsigned per = 16 / sizeof(T);
     const bool vec = sizeof(T) == 16 || L >= 1;
-    // gather with asynchronous copies: every copy of the tile is in flight at once
     if (vec) {
         for (unsigned p = threadIdx.x; p < Nt / per; p += NT) {
             const unsigned l = p * per;
@@ -419,13 +434,12 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
     }
     cp_async_wait_all();
     __syncthreads();
-    const T *mats = reinterpret_cast<const T *>(a.mats);
+    if (status) return;  // a failed assertion earlier on this stream: leave the state
     for (uint32_t i = 0; i < a.n_ops; i++) {
-        const DevOp op = load_op(a.ops + i);
-        apply_op<T, NT, KMAX>(tile, a.m, op, mats, mbuf);
+        const DevOp op = ops_s[i];
+        apply_op<T, NT, KMAX, false>(tile, a.m, op, mats_s, nullptr);
         __syncthreads();
     }
-    __syncthreads();
     if (vec) {
         for (unsigned p = threadIdx.x; p < Nt / per; p += NT) {
             const unsigned l = p * per;
@@ -700,16 +714,26 @@ cudaError_t setup_kernels() {
 
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
                              uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
-                             const MeasCtl *ctl, cudaStream_t s) {
+                             uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
+                             cudaStream_t s) {
+    if (n_ops > (uint32_t)kPassOps || mat_count > (uint32_t)kPassMats || m > 15 || n - m > 48)
+        return cudaErrorInvalidValue;
     TileArgs a;
     a.state = state;
     a.ops = ops;
     a.mats = mats;
     a.ctl = ctl;
-    a.tile_mask = tile_mask;
     a.n_ops = n_ops;
+    a.mat_first = mat_first;
+    a.mat_count = mat_count;
     a.n = n;
     a.m = m;
+    int t = 0, u = 0;
+    for (int b = 0; b < n; b++) {
+        if ((tile_mask >> b) & 1ull) a.tq[t++] = (uint8_t)b;
+        else a.ntq[u++] = (uint8_t)b;
+    }
+    if (t != m) return cudaErrorInvalidValue;
     // contiguous low qubits of the tile (the coalesced run length), capped at
     // 128-byte runs; a pass may lack them when its first op needs the room
     int low = __builtin_ctzll(~tile_mask);
@@ -717,8 +741,7 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
     a.L = low < cap ? low : cap;
     if (a.L > m) a.L = m;
     const unsigned grid = 1u << (n - m);
-    const size_t es = dtype == 0 ? 8 : 16;
-    const size_t smem = (es << m) + (kmax > 2 ? es * 32 * 32 : 0);  // + staging of a k >= 3 matrix
+    const size_t smem = tile_smem_bytes(dtype, m);
     if (kmax > 2) {
         if (dtype == 0) k_tile_pass<float, 256, 5><<<grid, 256, smem, s>>>(a);
         else k_tile_pass<double, 256, 5><<<grid, 256, smem, s>>>(a);
@@ -730,6 +753,11 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
         else k_tile_pass<double, 256, 2><<<grid, 256, smem, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+size_t tile_smem_bytes(int dtype, int m) {
+    const size_t es = dtype == 0 ? 8 : 16;
+    return (es << m) + es * kPassMats + sizeof(DevOp) * kPassOps;
 }
 
 cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s) {

@@ -75,11 +75,19 @@ cudaError_t setup_kernels();
 size_t resident_smem_bytes(int dtype, int n);
 int max_resident_bits(int dtype);
 
-// kmax: largest op size (qubits) in the launched ops; <= 2 selects the
-// register-lean instantiation without the k >= 3 paths.
+// Per-pass limits of the tile kernel: the pass's ops and coefficients are
+// copied into shared memory next to the tile.
+constexpr int kPassOps = 256;
+constexpr int kPassMats = 1024;  // complex values (one 5-qubit block, or 64 C2)
+size_t tile_smem_bytes(int dtype, int m);
+
+// One tile pass over ops[0, n_ops) whose coefficients are mats[mat_first,
+// mat_first + mat_count) (op.mat relative to mat_first).  kmax: largest dense
+// op (qubits); <= 2 selects the register-lean build without k >= 3 paths.
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
                              uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
-                             const MeasCtl *ctl, cudaStream_t s);
+                             uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
+                             cudaStream_t s);
 cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s);
 cudaError_t launch_resident_batch(int dtype, int threads, const Instance *d_insts, int count,
                                   int max_n, cudaStream_t s);

@@ -250,6 +250,48 @@ QSIM_API qsim_status qsim_sync(qsim_ctx *ctx);
 QSIM_API const char *qsim_last_error(const qsim_ctx *ctx);
 QSIM_API const char *qsim_status_string(qsim_status s);
 
+/* ---------------------------------------------------------------- batches --
+ * Many independent state vectors (for example one circuit structure with many
+ * parameter sets, or circuits of uneven width) advanced together.  Each
+ * instance i has n_qubits[i] qubits and its own compiled program (fused as in
+ * Section "Gate Fusion", passes as for qsim_apply), seed and measurement log.
+ * qsim_batch_run resets every state to |0...0> and runs every program: all
+ * instances whose state fits one block's shared memory (n <= 14 for C64,
+ * n <= 13 for C128, unless tile_bits forces tiling) run in ONE kernel launch,
+ * one block per instance, with their measurements inside the kernel; larger
+ * instances run their tile passes concurrently on per-instance streams that
+ * fork from and join back to the batch stream.  Asynchronous.
+ * Memory: as for qsim_create (alloc/free hooks or cudaMallocAsync).  Argument
+ * errors return QSIM_E_INVAL with nothing enqueued. */
+typedef struct qsim_batch qsim_batch;
+QSIM_API qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dtype,
+                                       void *stream, qsim_alloc_fn alloc, qsim_free_fn free_fn,
+                                       void *user, qsim_batch **out);
+QSIM_API qsim_status qsim_batch_destroy(qsim_batch *b);
+QSIM_API qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg);
+/* seeds[i]: draw seed of instance i (default 0). */
+QSIM_API qsim_status qsim_batch_set_seeds(qsim_batch *b, const uint64_t *seeds);
+/* Compile gates for instance `index` (host compiler) and upload the program,
+ * replacing any earlier one.  Synchronous on the host compile only. */
+QSIM_API qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *gates,
+                                        size_t n_gates, const double *mats, size_t n_mats);
+QSIM_API qsim_status qsim_batch_run(qsim_batch *b);
+/* Expectation values for every instance: instance i uses terms
+ * [term_offsets[i], term_offsets[i+1]) and writes out[t] = coef_t * Re <psi_i|P_t|psi_i>
+ * for those t (FP64 accumulation, definition as qsim_expect).  Synchronises. */
+QSIM_API qsim_status qsim_batch_expect(qsim_batch *b, const qsim_pauli_term *terms,
+                                       const uint64_t *term_offsets, double *out);
+/* State of instance `index` (bytes = 2^n * element size).  Synchronises. */
+QSIM_API qsim_status qsim_batch_state(qsim_batch *b, int index, void *dst, size_t bytes,
+                                      int dst_is_device);
+/* Outcome log of instance `index` since the last qsim_batch_run (as
+ * qsim_outcomes).  Synchronises; returns QSIM_E_ZEROPROB if that instance's
+ * assertion failed. */
+QSIM_API qsim_status qsim_batch_outcomes(qsim_batch *b, int index, int32_t *outcomes, double *probs,
+                                         size_t cap, size_t *n_total);
+/* Number of instances run resident (one block each, one launch) by qsim_batch_run. */
+QSIM_API qsim_status qsim_batch_resident_count(const qsim_batch *b, int *count);
+
 /* ------------------------------------------------ no-allocation variant --
  * The paper has no counterpart to this entry point; it serves callers that
  * own a state vector in device memory but may not allocate device memory

@@ -218,7 +218,7 @@ Staging *get_staging(qsim_ctx *c, size_t bytes) {
             }
     }
     Staging s;
-    s.bytes = std::max(bytes, (size_t)1 << 22);
+    s.bytes = std::max(bytes, (size_t)1 << 20);
     if (cudaHostAlloc(&s.host, s.bytes, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -349,9 +349,11 @@ qsim_status launch_measure(qsim_ctx *c, int q, int mode, int reset, uint64_t see
 }
 
 qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
-    // 512 threads per tile for complex64 (more warps in flight per SM); the
-    // complex128 tile kernel keeps 256 (its 512-thread build spills)
-    const int threads = c->cfg.threads ? c->cfg.threads : (c->dtype == QSIM_C64 ? 512 : 256);
+    // 512 threads per tile for complex64 rotation passes (more warps in flight);
+    // dense C2 passes and complex128 keep 256 (their 512-thread builds are capped
+    // at 64 registers and lose more to spills than they gain)
+    const int threads = c->cfg.threads ? c->cfg.threads
+                                       : (c->dtype == QSIM_C64 && c->cfg.fusion == 2 ? 512 : 256);
     if (dc.resident) {
         qsim_status s = ensure_log(c, c->log_n + dc.measurements);
         if (s != QSIM_OK) return s;
@@ -369,7 +371,7 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
         in.log = c->log;
         in.thr = c->thr;
         in.n = c->n;
-        if (dc.n_ops) CK(qsim::launch_resident(c->dtype, threads, in, c->stream), "resident launch");
+        if (dc.n_ops) CK(qsim::launch_resident(c->dtype, dc.kmax, in, c->stream), "resident launch");
         c->ordinal += dc.measurements;
         c->log_n += dc.measurements;
         return QSIM_OK;
@@ -947,6 +949,356 @@ qsim_status qsim_schedule(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng
         out_first[i] = hp.passes[i].first;
         out_count[i] = hp.passes[i].count;
     }
+    return QSIM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches --
+// A batch is a set of ordinary contexts (one per instance: state, control
+// block, log) plus the launch plan: instances that fit one block's shared
+// memory run together in one resident launch per (width, op size) group on the
+// batch stream; the others run their tile passes on their own streams, forked
+// from and joined back to the batch stream.
+struct qsim_batch {
+    int count = 0;
+    qsim_dtype dtype = QSIM_C64;
+    cudaStream_t stream = nullptr;
+    std::vector<qsim_ctx *> inst;
+    std::vector<std::vector<DevChunk>> prog;
+    std::vector<char> resident;
+    std::vector<cudaStream_t> own;  // non-resident instances only
+    std::vector<cudaEvent_t> done;  // non-resident instances only
+    cudaEvent_t fork = nullptr;
+    qsim_ctx *aux = nullptr;        // staging and scratch on the batch stream
+    qsim::Instance *d_insts = nullptr;
+    size_t insts_cap = 0;
+    MeasCtl *h_init = nullptr;      // pinned cleared control block
+    std::string err;
+};
+
+namespace {
+
+qsim_status bfail(qsim_batch *b, qsim_status s, const std::string &msg) {
+    if (b) b->err = msg;
+    g_err = msg;
+    return s;
+}
+
+// |0...0> and a cleared control block, enqueued on the context's stream.
+qsim_status reset_async(qsim_ctx *c, const MeasCtl *h_init) {
+    CK(qsim::launch_set_basis(c->dtype, c->state, c->n, 0, c->stream), "state reset");
+    CK(cudaMemcpyAsync(c->ctl, h_init, sizeof(MeasCtl), cudaMemcpyHostToDevice, c->stream),
+       "control reset");
+    c->ordinal = 0;
+    c->log_n = 0;
+    return QSIM_OK;
+}
+
+void release_instance_program(qsim_batch *b, int i) {
+    for (auto &dc : b->prog[i]) release_chunk(b->inst[i], dc);
+    b->prog[i].clear();
+}
+
+// fork: `s` waits for everything enqueued so far on the batch stream
+qsim_status fork_to(qsim_batch *b, cudaStream_t s) {
+    qsim_ctx *c = b->aux;
+    CK(cudaEventRecord(b->fork, b->stream), "fork event");
+    CK(cudaStreamWaitEvent(s, b->fork, 0), "fork wait");
+    return QSIM_OK;
+}
+
+qsim_status join_from(qsim_batch *b, int i) {
+    qsim_ctx *c = b->aux;
+    CK(cudaEventRecord(b->done[i], b->own[i]), "join event");
+    CK(cudaStreamWaitEvent(b->stream, b->done[i], 0), "join wait");
+    return QSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qsim_status qsim_batch_destroy(qsim_batch *b) {
+    if (!b) return QSIM_OK;
+    if (b->stream || true) cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < b->count; i++) {
+        if (b->own[i]) cudaStreamSynchronize(b->own[i]);
+        if (b->inst[i]) {
+            release_instance_program(b, i);
+            qsim_destroy(b->inst[i]);
+        }
+        if (b->done[i]) cudaEventDestroy(b->done[i]);
+        if (b->own[i]) cudaStreamDestroy(b->own[i]);
+    }
+    if (b->aux) {
+        dfree(b->aux, b->d_insts, b->insts_cap * sizeof(qsim::Instance));
+        qsim_destroy(b->aux);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->h_init) cudaFreeHost(b->h_init);
+    cudaGetLastError();
+    delete b;
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dtype, void *stream,
+                              qsim_alloc_fn alloc, qsim_free_fn free_fn, void *user, qsim_batch **out) {
+    if (!out) return fail(nullptr, QSIM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (count <= 0 || !n_qubits) return fail(nullptr, QSIM_E_INVAL, "count must be > 0 with n_qubits given");
+    for (int i = 0; i < count; i++)
+        if (n_qubits[i] < 1 || n_qubits[i] > 34) return fail(nullptr, QSIM_E_INVAL, "n_qubits must be in [1, 34]");
+    auto b = std::make_unique<qsim_batch>();
+    b->count = count;
+    b->dtype = dtype;
+    b->stream = (cudaStream_t)stream;
+    b->inst.assign(count, nullptr);
+    b->prog.resize(count);
+    b->resident.assign(count, 0);
+    b->own.assign(count, nullptr);
+    b->done.assign(count, nullptr);
+    qsim_status s = qsim_create(1, dtype, stream, alloc, free_fn, user, &b->aux);
+    if (s != QSIM_OK) return s;
+    if (cudaMallocHost((void **)&b->h_init, sizeof(MeasCtl)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        qsim_batch_destroy(b.release());
+        return fail(nullptr, QSIM_E_OOM, "batch host resources");
+    }
+    std::memset(b->h_init, 0, sizeof(MeasCtl));
+    b->h_init->success = 1.0;
+    const int mx = qsim::max_resident_bits(dtype);
+    for (int i = 0; i < count; i++) {
+        const int n = n_qubits[i];
+        s = qsim_create(n, dtype, stream, alloc, free_fn, user, &b->inst[i]);
+        if (s != QSIM_OK) {
+            qsim_batch_destroy(b.release());
+            return s;
+        }
+        if (n <= mx) {
+            b->resident[i] = 1;
+            b->inst[i]->cfg.tile_bits = n;  // the whole state in one block
+        } else {
+            if (cudaStreamCreateWithFlags(&b->own[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                qsim_batch_destroy(b.release());
+                return fail(nullptr, QSIM_E_CUDA, "instance stream");
+            }
+            b->inst[i]->stream = b->own[i];  // qsim_create synchronised its allocations
+        }
+    }
+    *out = b.release();
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg) {
+    if (!b || !cfg) return bfail(b, QSIM_E_INVAL, "null argument");
+    for (int i = 0; i < b->count; i++) {
+        qsim_config c2 = *cfg;
+        if (b->resident[i]) c2.tile_bits = b->inst[i]->n;  // residency is fixed at create
+        qsim_status s = qsim_set_config(b->inst[i], &c2);
+        if (s != QSIM_OK) return bfail(b, s, b->inst[i]->err);
+    }
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_set_seeds(qsim_batch *b, const uint64_t *seeds) {
+    if (!b || !seeds) return bfail(b, QSIM_E_INVAL, "null argument");
+    for (int i = 0; i < b->count; i++) b->inst[i]->seed = seeds[i];
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *g, size_t ng,
+                               const double *mats, size_t nm) {
+    if (!b || index < 0 || index >= b->count) return bfail(b, QSIM_E_INVAL, "bad batch index");
+    qsim_ctx *c = b->inst[index];
+    if (ng && !g) return bfail(b, QSIM_E_INVAL, "gates is NULL");
+    std::string err;
+    if (!qsim::validate(c->n, g, ng, mats, nm, err)) return bfail(b, QSIM_E_INVAL, err);
+    release_instance_program(b, index);
+    // programs live on the batch stream (aux): uploaded before, freed after, every run
+    auto sink = [&](const Packed &pk) -> qsim_status {
+        DevChunk dc;
+        qsim_status st = upload_chunk(b->aux, pk, dc);
+        if (st != QSIM_OK) {
+            release_chunk(b->aux, dc);
+            return st;
+        }
+        b->prog[index].push_back(std::move(dc));
+        return QSIM_OK;
+    };
+    qsim_status s;
+    if (b->resident[index]) {  // the resident kernel walks one contiguous program
+        HostProgram hp;
+        qsim::compile(c->n, c->dtype, c->cfg, g, ng, mats, nm, hp);
+        Packed pk;
+        pack(hp, c->dtype, pk);
+        s = sink(pk);
+    } else {
+        s = compile_chunks(c, g, ng, mats, nm, sink);
+    }
+    if (s != QSIM_OK) {
+        release_instance_program(b, index);
+        return bfail(b, s, b->aux->err);
+    }
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_run(qsim_batch *b) {
+    if (!b) return fail(nullptr, QSIM_E_INVAL, "null batch");
+    qsim_ctx *c = b->aux;
+    // resident instances, grouped by (width, largest op) so that each launch
+    // sizes its shared memory for its own width
+    std::vector<qsim::Instance> insts;
+    std::vector<std::pair<std::pair<int, int>, size_t>> groups;  // ((n, kmax), first)
+    std::vector<int> order;
+    for (int i = 0; i < b->count; i++)
+        if (b->resident[i]) order.push_back(i);
+    auto kmax_of = [&](int i) { return b->prog[i].empty() ? 1 : b->prog[i][0].kmax; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int nx = b->inst[x]->n, ny = b->inst[y]->n;
+        return nx != ny ? nx < ny : (kmax_of(x) > 2) < (kmax_of(y) > 2);
+    });
+    for (int i : order) {
+        qsim_ctx *ic = b->inst[i];
+        const DevChunk *dc = b->prog[i].empty() ? nullptr : &b->prog[i][0];
+        const uint64_t meas = dc ? dc->measurements : 0;
+        qsim_status s = ensure_log(ic, meas);
+        if (s != QSIM_OK) return bfail(b, s, ic->err);
+        qsim::Instance in;
+        std::memset(&in, 0, sizeof(in));
+        in.state = ic->state;
+        in.ops = dc ? dc->d_ops : nullptr;
+        in.mats = dc ? dc->d_mats : nullptr;
+        in.n_ops = dc ? dc->n_ops : 0;
+        in.seed = ic->seed;
+        in.log_cap = ic->log_cap;
+        in.ctl = ic->ctl;
+        in.log = ic->log;
+        in.thr = ic->thr;
+        in.n = ic->n;
+        in.flags = qsim::kInstInit;
+        const std::pair<int, int> key(ic->n, kmax_of(i) > 2 ? 5 : 2);
+        if (groups.empty() || groups.back().first != key) groups.emplace_back(key, insts.size());
+        insts.push_back(in);
+        ic->ordinal = meas;
+        ic->log_n = meas;
+    }
+    if (!insts.empty()) {
+        if (insts.size() > b->insts_cap) {
+            dfree(c, b->d_insts, b->insts_cap * sizeof(qsim::Instance));
+            b->insts_cap = std::max(insts.size(), (size_t)64);
+            b->d_insts = (qsim::Instance *)dalloc(c, b->insts_cap * sizeof(qsim::Instance));
+            if (!b->d_insts) {
+                b->insts_cap = 0;
+                return bfail(b, QSIM_E_OOM, "instance table");
+            }
+        }
+        qsim_status s = upload(c, b->d_insts, insts.data(), insts.size() * sizeof(qsim::Instance));
+        if (s != QSIM_OK) return bfail(b, s, c->err);
+        for (size_t gi = 0; gi < groups.size(); gi++) {
+            const size_t first = groups[gi].second;
+            const size_t last = gi + 1 < groups.size() ? groups[gi + 1].second : insts.size();
+            CK(qsim::launch_resident_batch(b->dtype, groups[gi].first.second, b->d_insts + first,
+                                           (int)(last - first), groups[gi].first.first, b->stream),
+               "resident batch launch");
+        }
+    }
+    // tiled instances: concurrent on their own streams
+    for (int i = 0; i < b->count; i++) {
+        if (b->resident[i]) continue;
+        qsim_ctx *ic = b->inst[i];
+        qsim_status s = fork_to(b, b->own[i]);
+        if (s == QSIM_OK) s = reset_async(ic, b->h_init);
+        for (size_t k = 0; s == QSIM_OK && k < b->prog[i].size(); k++) s = launch_chunk(ic, b->prog[i][k]);
+        if (s == QSIM_OK) s = join_from(b, i);
+        if (s != QSIM_OK) return bfail(b, s, ic->err);
+    }
+    return QSIM_OK;
+}
+
+qsim_status qsim_batch_expect(qsim_batch *b, const qsim_pauli_term *terms, const uint64_t *off,
+                              double *out) {
+    if (!b || !off) return fail(nullptr, QSIM_E_INVAL, "null argument");
+    qsim_ctx *c = b->aux;
+    const uint64_t total = off[b->count];
+    if (total && (!terms || !out)) return bfail(b, QSIM_E_INVAL, "null terms or out");
+    for (int i = 0; i < b->count; i++) {
+        if (off[i + 1] < off[i]) return bfail(b, QSIM_E_INVAL, "term offsets must not decrease");
+        const int n = b->inst[i]->n;
+        const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+        for (uint64_t t = off[i]; t < off[i + 1]; t++)
+            if ((terms[t].x_mask | terms[t].z_mask) & ~full)
+                return bfail(b, QSIM_E_INVAL, "Pauli term beyond the instance's qubits");
+    }
+    if (total == 0) return QSIM_OK;
+    const size_t tb = total * 3 * sizeof(uint64_t);
+    uint64_t *d_terms = (uint64_t *)dalloc(c, tb);
+    double *d_out = (double *)dalloc(c, total * sizeof(double));
+    std::vector<qsim::ExpectJob> jobs;
+    for (int i = 0; i < b->count; i++) {
+        if (!b->resident[i] || off[i + 1] == off[i]) continue;
+        qsim::ExpectJob j;
+        j.state = b->inst[i]->state;
+        j.terms = d_terms + 3 * off[i];
+        j.out = d_out + off[i];
+        j.n_terms = (uint32_t)(off[i + 1] - off[i]);
+        j.n = b->inst[i]->n;
+        jobs.push_back(j);
+    }
+    qsim::ExpectJob *d_jobs = (qsim::ExpectJob *)dalloc(c, std::max<size_t>(jobs.size(), 1) * sizeof(qsim::ExpectJob));
+    qsim_status s = (d_terms && d_out && d_jobs) ? QSIM_OK : bfail(b, QSIM_E_OOM, "expectation buffers");
+    if (s == QSIM_OK) s = upload(c, d_terms, terms, tb);
+    if (s == QSIM_OK && !jobs.empty()) s = upload(c, d_jobs, jobs.data(), jobs.size() * sizeof(qsim::ExpectJob));
+    if (s == QSIM_OK && !jobs.empty()) {
+        cudaError_t e = qsim::launch_expect_batch(b->dtype, d_jobs, (int)jobs.size(), b->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "batched expectation launch");
+    }
+    for (int i = 0; s == QSIM_OK && i < b->count; i++) {
+        if (b->resident[i] || off[i + 1] == off[i]) continue;
+        qsim_ctx *ic = b->inst[i];
+        const size_t nt = off[i + 1] - off[i];
+        s = fork_to(b, b->own[i]);
+        if (s == QSIM_OK) s = ensure_partials(ic, (size_t)qsim::expect_blocks(ic->n) * nt);
+        if (s == QSIM_OK) {
+            cudaError_t e = qsim::launch_expect(b->dtype, ic->state, ic->n, d_terms + 3 * off[i], nt,
+                                                ic->partials, d_out + off[i], ic->stream);
+            if (e != cudaSuccess) s = cuda_fail(ic, e, "expectation launch");
+        }
+        if (s == QSIM_OK) s = join_from(b, i);
+    }
+    if (s == QSIM_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, d_out, total * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "expectation readback");
+    }
+    dfree(c, d_terms, tb);
+    dfree(c, d_out, total * sizeof(double));
+    dfree(c, d_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(qsim::ExpectJob));
+    return s == QSIM_OK ? QSIM_OK : bfail(b, s, c->err);
+}
+
+qsim_status qsim_batch_state(qsim_batch *b, int index, void *dst, size_t bytes, int dst_is_device) {
+    if (!b || index < 0 || index >= b->count) return bfail(b, QSIM_E_INVAL, "bad batch index");
+    return qsim_state(b->inst[index], dst, bytes, dst_is_device);
+}
+
+qsim_status qsim_batch_outcomes(qsim_batch *b, int index, int32_t *outcomes, double *probs, size_t cap,
+                                size_t *n_total) {
+    if (!b || index < 0 || index >= b->count) return bfail(b, QSIM_E_INVAL, "bad batch index");
+    qsim_ctx *ic = b->inst[index];
+    qsim_status s = qsim_outcomes(ic, outcomes, probs, cap, n_total);
+    if (s != QSIM_OK) return s;
+    return sync_read(ic);
+}
+
+qsim_status qsim_batch_resident_count(const qsim_batch *b, int *count) {
+    if (!b || !count) return QSIM_E_INVAL;
+    int k = 0;
+    for (int i = 0; i < b->count; i++) k += b->resident[i];
+    *count = k;
     return QSIM_OK;
 }
 

@@ -452,23 +452,39 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
 }
 
 // -------------------------------------------------------------- resident --
-template <typename T, int NT>
+template <typename T, int NT, int KMAX>
 __device__ void run_resident(const Instance &in, T *tile, double *red, int *bcast, double *bscale,
                              int max_n) {
     const int n = in.n;
     const unsigned N = 1u << n;
     T *mbuf = tile + (1u << max_n);
     T *st = reinterpret_cast<T *>(in.state);
-    if (in.ctl->status) return;
-    for (unsigned l = threadIdx.x; l < N; l += NT) tile[l] = st[l];
+    if (in.flags & kInstInit) {
+        // start from |0...0> with a cleared control block: no state read at all
+        for (unsigned l = threadIdx.x; l < N; l += NT) {
+            T v = czero(tile[0]);
+            if (l == 0) v.x = 1;
+            tile[l] = v;
+        }
+        if (threadIdx.x == 0) {
+            in.ctl->status = 0;
+            in.ctl->success = 1.0;
+            in.ctl->arrive = 0;
+        }
+    } else {
+        if (in.ctl->status) return;
+        for (unsigned l = threadIdx.x; l < N; l += NT) tile[l] = st[l];
+    }
     __syncthreads();
     const T *mats = reinterpret_cast<const T *>(in.mats);
     uint64_t ev = 0;
     bool failed = false;
+    DevOp nxt = load_op(in.ops);
     for (uint64_t i = 0; i < in.n_ops; i++) {
-        const DevOp op = load_op(in.ops + i);
+        const DevOp op = nxt;
+        if (i + 1 < in.n_ops) nxt = load_op(in.ops + i + 1);  // in flight while op runs
         if (op.k) {
-            apply_op<T, NT, 5>(tile, n, op, mats, mbuf);
+            apply_op<T, NT, KMAX>(tile, n, op, mats, mbuf);
             __syncthreads();
             continue;
         }
@@ -528,17 +544,17 @@ __device__ void run_resident(const Instance &in, T *tile, double *red, int *bcas
     for (unsigned l = threadIdx.x; l < N; l += NT) st[l] = tile[l];
 }
 
-template <typename R, int NT>
+template <typename R, int NT, int KMAX>
 __global__ void __launch_bounds__(NT) k_resident_one(Instance in) {
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2 * NT / 32];
     __shared__ int bcast[1];
     __shared__ double bscale[1];
-    run_resident<T, NT>(in, reinterpret_cast<T *>(smem_raw), red, bcast, bscale, in.n);
+    run_resident<T, NT, KMAX>(in, reinterpret_cast<T *>(smem_raw), red, bcast, bscale, in.n);
 }
 
-template <typename R, int NT>
+template <typename R, int NT, int KMAX>
 __global__ void __launch_bounds__(NT) k_resident_batch(const Instance *insts, int max_n) {
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -546,7 +562,7 @@ __global__ void __launch_bounds__(NT) k_resident_batch(const Instance *insts, in
     __shared__ int bcast[1];
     __shared__ double bscale[1];
     const Instance in = insts[blockIdx.x];
-    run_resident<T, NT>(in, reinterpret_cast<T *>(smem_raw), red, bcast, bscale, max_n);
+    run_resident<T, NT, KMAX>(in, reinterpret_cast<T *>(smem_raw), red, bcast, bscale, max_n);
 }
 
 // ----------------------------------------------------------- measurement --
@@ -659,6 +675,32 @@ __global__ void __launch_bounds__(256) k_expect(const void *state, int n, const 
     if (threadIdx.x == 0) partials[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
 }
 
+// Batched expectation: block b evaluates every term of job b over its (small)
+// state, each term a fixed-shape FP64 block reduction in index order per thread.
+template <typename R>
+__global__ void __launch_bounds__(256) k_expect_batch(const ExpectJob *jobs) {
+    using T = typename V2<R>::T;
+    __shared__ double red[2 * 256 / 32];
+    const ExpectJob jb = jobs[blockIdx.x];
+    const T *st = reinterpret_cast<const T *>(jb.state);
+    const uint64_t N = 1ull << jb.n;
+    for (uint32_t t = 0; t < jb.n_terms; t++) {
+        const uint64_t x = jb.terms[3 * t], z = jb.terms[3 * t + 1];
+        const int ny = __popcll(x & z) & 3;
+        double acc = 0, dummy = 0;
+        for (uint64_t j = threadIdx.x; j < N; j += 256) {
+            const double2 aj = to_d(st[j]), ax = to_d(st[j ^ x]);
+            const double wr = ax.x * aj.x + ax.y * aj.y;
+            const double wi = ax.x * aj.y - ax.y * aj.x;
+            double v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
+            if (__popcll(j & z) & 1) v = -v;
+            acc += v;
+        }
+        block_sum2<256>(acc, dummy, red);
+        if (threadIdx.x == 0) jb.out[t] = __longlong_as_double((long long)jb.terms[3 * t + 2]) * acc;
+    }
+}
+
 __global__ void k_expect_final(const uint64_t *terms, size_t n_terms, int P, const double *partials,
                                double *out) {
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -704,10 +746,14 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 512, 2>));
     QSIM_ATTR((k_tile_pass<float, 256, 5>));
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
-    QSIM_ATTR((k_resident_one<float, 256>));
-    QSIM_ATTR((k_resident_one<double, 256>));
-    QSIM_ATTR((k_resident_batch<float, 256>));
-    QSIM_ATTR((k_resident_batch<double, 256>));
+    QSIM_ATTR((k_resident_one<float, 256, 2>));
+    QSIM_ATTR((k_resident_one<double, 256, 2>));
+    QSIM_ATTR((k_resident_batch<float, 256, 2>));
+    QSIM_ATTR((k_resident_batch<double, 256, 2>));
+    QSIM_ATTR((k_resident_one<float, 256, 5>));
+    QSIM_ATTR((k_resident_one<double, 256, 5>));
+    QSIM_ATTR((k_resident_batch<float, 256, 5>));
+    QSIM_ATTR((k_resident_batch<double, 256, 5>));
 #undef QSIM_ATTR
     return cudaSuccess;
 }
@@ -760,20 +806,29 @@ size_t tile_smem_bytes(int dtype, int m) {
     return (es << m) + es * kPassMats + sizeof(DevOp) * kPassOps;
 }
 
-cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s) {
-    (void)threads;
+cudaError_t launch_resident(int dtype, int kmax, const Instance &inst, cudaStream_t s) {
     const size_t smem = resident_smem_bytes(dtype, inst.n);
-    if (dtype == 0) k_resident_one<float, 256><<<1, 256, smem, s>>>(inst);
-    else k_resident_one<double, 256><<<1, 256, smem, s>>>(inst);
+    if (kmax > 2) {
+        if (dtype == 0) k_resident_one<float, 256, 5><<<1, 256, smem, s>>>(inst);
+        else k_resident_one<double, 256, 5><<<1, 256, smem, s>>>(inst);
+    } else {
+        if (dtype == 0) k_resident_one<float, 256, 2><<<1, 256, smem, s>>>(inst);
+        else k_resident_one<double, 256, 2><<<1, 256, smem, s>>>(inst);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_resident_batch(int dtype, int threads, const Instance *d_insts, int count,
+cudaError_t launch_resident_batch(int dtype, int kmax, const Instance *d_insts, int count,
                                   int max_n, cudaStream_t s) {
-    (void)threads;
+    if (count <= 0) return cudaSuccess;
     const size_t smem = resident_smem_bytes(dtype, max_n);
-    if (dtype == 0) k_resident_batch<float, 256><<<count, 256, smem, s>>>(d_insts, max_n);
-    else k_resident_batch<double, 256><<<count, 256, smem, s>>>(d_insts, max_n);
+    if (kmax > 2) {
+        if (dtype == 0) k_resident_batch<float, 256, 5><<<count, 256, smem, s>>>(d_insts, max_n);
+        else k_resident_batch<double, 256, 5><<<count, 256, smem, s>>>(d_insts, max_n);
+    } else {
+        if (dtype == 0) k_resident_batch<float, 256, 2><<<count, 256, smem, s>>>(d_insts, max_n);
+        else k_resident_batch<double, 256, 2><<<count, 256, smem, s>>>(d_insts, max_n);
+    }
     return cudaGetLastError();
 }
 
@@ -807,6 +862,13 @@ cudaError_t launch_prob_only(int dtype, const void *state, int n, int q, double 
     a.q = q;
     if (dtype == 0) k_prob<float, false><<<P, kRedThreads, 0, s>>>(state, n, a, partials, ctl, nullptr);
     else k_prob<double, false><<<P, kRedThreads, 0, s>>>(state, n, a, partials, ctl, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expect_batch(int dtype, const ExpectJob *d_jobs, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (dtype == 0) k_expect_batch<float><<<count, 256, 0, s>>>(d_jobs);
+    else k_expect_batch<double><<<count, 256, 0, s>>>(d_jobs);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,17 @@ struct Instance {
     MeasRec *log;
     double thr;
     int32_t n;
-    int32_t pad;
+    uint32_t flags;        // kInstInit: start from |0...0> and a cleared control block
+};
+constexpr uint32_t kInstInit = 1;
+
+// One batched expectation job: terms (x, z, coef bits) of one state.
+struct ExpectJob {
+    const void *state;
+    const uint64_t *terms;
+    double *out;
+    uint32_t n_terms;
+    int32_t n;
 };
 
 struct MeasArgs {
@@ -88,8 +98,10 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
                              uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
                              uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
                              cudaStream_t s);
-cudaError_t launch_resident(int dtype, int threads, const Instance &inst, cudaStream_t s);
-cudaError_t launch_resident_batch(int dtype, int threads, const Instance *d_insts, int count,
+// Resident whole-state interpreter; kmax as for launch_tile_pass.  The batch
+// form runs one block per instance, shared memory sized for max_n qubits.
+cudaError_t launch_resident(int dtype, int kmax, const Instance &inst, cudaStream_t s);
+cudaError_t launch_resident_batch(int dtype, int kmax, const Instance *d_insts, int count,
                                   int max_n, cudaStream_t s);
 // Grid size (blocks) the probability reduction uses for an n-qubit state;
 // partials must hold that many double2.
@@ -99,6 +111,8 @@ cudaError_t launch_measure(int dtype, void *state, int n, const MeasArgs &a, dou
 // Born probabilities only (no draw, no collapse): writes ctl->p0, ctl->p1.
 cudaError_t launch_prob_only(int dtype, const void *state, int n, int q, double *partials,
                              MeasCtl *ctl, cudaStream_t s);
+// One block per job (states of <= 14 qubits): every term of the job in turn.
+cudaError_t launch_expect_batch(int dtype, const ExpectJob *d_jobs, int count, cudaStream_t s);
 int expect_blocks(int n);
 cudaError_t launch_expect(int dtype, const void *state, int n, const uint64_t *d_terms,
                           size_t n_terms, double *partials, double *d_out, cudaStream_t s);

@@ -71,6 +71,16 @@ _SIGS = {
     "qsim_reset_state": ([_vp], _i32),
     "qsim_state_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)], _i32),
     "qsim_sync": ([_vp], _i32),
+    "qsim_batch_create": ([_i32, _vp, _i32, _vp, ALLOC_FN, FREE_FN, _vp, ctypes.POINTER(_vp)], _i32),
+    "qsim_batch_destroy": ([_vp], _i32),
+    "qsim_batch_set_config": ([_vp, ctypes.POINTER(QsimConfig)], _i32),
+    "qsim_batch_set_seeds": ([_vp, _vp], _i32),
+    "qsim_batch_compile": ([_vp, _i32, _vp, _sz, _vp, _sz], _i32),
+    "qsim_batch_run": ([_vp], _i32),
+    "qsim_batch_expect": ([_vp, _vp, _vp, _vp], _i32),
+    "qsim_batch_state": ([_vp, _i32, _vp, _sz, _i32], _i32),
+    "qsim_batch_outcomes": ([_vp, _i32, _vp, _vp, _sz, ctypes.POINTER(_sz)], _i32),
+    "qsim_batch_resident_count": ([_vp, ctypes.POINTER(_i32)], _i32),
     "qsim_profile_start": ([_vp, _i32], _i32),
     "qsim_profile_read": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_u64), ctypes.POINTER(_dbl),
                            ctypes.POINTER(_dbl), ctypes.POINTER(_u64)], _i32),
@@ -311,6 +321,87 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             _lib.qsim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent states advanced together (see qsim_batch_* in qsim.h)."""
+
+    def __init__(self, n_qubits, dtype: str = "c64", stream=None, torch_memory: bool = True,
+                 config: Optional[dict] = None, seeds=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.n = [int(x) for x in n_qubits]
+        self.dtype = C64 if dtype in ("c64", C64) else C128
+        self.np_dtype = np.complex64 if self.dtype == C64 else np.complex128
+        self.device = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self._alloc = _TorchAllocator(self.device) if torch_memory else None
+        nq = np.asarray(self.n, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(_lib.qsim_batch_create(len(self.n), _ptr(nq), self.dtype, sp,
+                                      self._alloc.alloc if self._alloc else ALLOC_FN(),
+                                      self._alloc.free if self._alloc else FREE_FN(), None,
+                                      ctypes.byref(h)))
+        self.h = h
+        if config:
+            _check(_lib.qsim_batch_set_config(self.h, ctypes.byref(make_config(**config))))
+        if seeds is not None:
+            s = np.ascontiguousarray(seeds, dtype=np.uint64)
+            _check(_lib.qsim_batch_set_seeds(self.h, _ptr(s)))
+
+    def __len__(self):
+        return len(self.n)
+
+    def compile(self, index: int, gates, mats=None):
+        g = _gates(gates)
+        m = _mats(mats)
+        _check(_lib.qsim_batch_compile(self.h, index, _ptr(g), g.size, _ptr(m), m.size))
+
+    def run(self):
+        _check(_lib.qsim_batch_run(self.h))
+
+    def expect(self, term_lists):
+        """term_lists[i]: TERM_DTYPE array for instance i -> list of per-term values."""
+        arrs = [np.ascontiguousarray(t, dtype=TERM_DTYPE) for t in term_lists]
+        off = np.zeros(len(arrs) + 1, dtype=np.uint64)
+        off[1:] = np.cumsum([a.size for a in arrs])
+        allt = np.concatenate(arrs) if arrs else np.zeros(0, dtype=TERM_DTYPE)
+        out = np.zeros(max(int(off[-1]), 1), dtype=np.float64)
+        _check(_lib.qsim_batch_expect(self.h, _ptr(allt), _ptr(off), _ptr(out)))
+        return [out[int(off[i]):int(off[i + 1])].copy() for i in range(len(arrs))]
+
+    def state(self, index: int) -> np.ndarray:
+        a = np.zeros(1 << self.n[index], dtype=self.np_dtype)
+        _check(_lib.qsim_batch_state(self.h, index, _ptr(a), a.nbytes, 0))
+        return a
+
+    def outcomes(self, index: int):
+        n = ctypes.c_size_t()
+        st = _lib.qsim_batch_outcomes(self.h, index, None, None, 0, ctypes.byref(n))
+        k = n.value
+        oc = np.zeros(max(k, 1), dtype=np.int32)
+        pr = np.zeros(max(k, 1), dtype=np.float64)
+        st = _lib.qsim_batch_outcomes(self.h, index, _ptr(oc), _ptr(pr), k, ctypes.byref(n))
+        return oc[:k].copy(), pr[:k].copy(), st
+
+    def resident_count(self) -> int:
+        k = ctypes.c_int()
+        _check(_lib.qsim_batch_resident_count(self.h, ctypes.byref(k)))
+        return k.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qsim_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -356,3 +356,28 @@ def config_large(seed=3, target_gates=115_000_000, n_meas=8) -> Circuit:
     circuits carry 8 filtering measurements)."""
     return ucc_circuit(21, seed=seed, n_gadgets=2000, w_lo=2, w_hi=6, theta="uniform",
                        target_gates=target_gates, n_meas=n_meas)
+
+
+def config_batched(seed=4, n_param_sets=512, n_uneven=256, gates=20_000, n_terms=200,
+                   n_set_gadgets=1600):
+    """(i) n_param_sets parameter sets (theta ~ U(-pi, pi), set i drawn with seed
+    seed + i) of one 12-qubit UCC-style circuit structure (n_set_gadgets weight
+    2-6 gadgets, cycled to `gates`); (ii) n_uneven circuits of width uniform in
+    10..18 with `gates` gates each.  One random n_terms-term Hamiltonian per
+    instance (seed 10_000 + instance).  Returns (circuits, hamiltonians)."""
+    circuits = []
+    base = ucc_circuit(12, seed=seed, n_gadgets=n_set_gadgets, w_lo=2, w_hi=6, target_gates=gates)
+    rz = np.flatnonzero(base.gates["op"] == OP["RZ"])  # one RZ(2 theta) per gadget, in order
+    gadget_of_rz = np.arange(rz.size) % n_set_gadgets
+    for i in range(n_param_sets):
+        th = np.random.default_rng(seed + i).uniform(-math.pi, math.pi, size=n_set_gadgets)
+        g = base.gates.copy()
+        g["p"][rz, 0] = 2.0 * th[gadget_of_rz]
+        circuits.append(Circuit(12, g, None, seed=seed, param_set=i))
+    wrng = np.random.default_rng(seed + 77_777)
+    widths = wrng.integers(10, 19, size=n_uneven)
+    for j, n in enumerate(widths):
+        circuits.append(ucc_circuit(int(n), seed=seed + 100_000 + j, n_gadgets=None, w_lo=2, w_hi=6,
+                                    theta="uniform", target_gates=gates))
+    hams = [random_hamiltonian(c.n, n_terms, seed=10_000 + k) for k, c in enumerate(circuits)]
+    return circuits, hams

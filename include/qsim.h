@@ -260,7 +260,11 @@ QSIM_API const char *qsim_status_string(qsim_status s);
  * n <= 13 for C128, unless tile_bits forces tiling) run in ONE kernel launch,
  * one block per instance, with their measurements inside the kernel; larger
  * instances run their tile passes concurrently on per-instance streams that
- * fork from and join back to the batch stream.  Asynchronous.
+ * fork from and join back to the batch stream.  Asynchronous.  The first run
+ * after a compile, reconfiguration or reseeding is enqueued eagerly (and makes
+ * every allocation); the second is captured into a CUDA graph that it and all
+ * later runs launch with one call.  Each run restarts every state from
+ * |0...0>, so runs are identical.
  * Memory: as for qsim_create (alloc/free hooks or cudaMallocAsync).  Argument
  * errors return QSIM_E_INVAL with nothing enqueued. */
 typedef struct qsim_batch qsim_batch;

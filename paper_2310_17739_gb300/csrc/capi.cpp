@@ -975,6 +975,20 @@ struct qsim_batch {
     size_t insts_cap = 0;
     MeasCtl *h_init = nullptr;      // pinned cleared control block
     std::string err;
+    // run replay: after one eager run (which makes every allocation), the next
+    // run is captured into a CUDA graph and later runs replay it with one launch;
+    // compiling, reconfiguring or reseeding any instance drops the graph
+    int eager_runs = 0;
+    std::vector<uint64_t> meas_after;  // log records per instance after one run
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
+        eager_runs = 0;
+    }
 };
 
 namespace {
@@ -1021,7 +1035,8 @@ extern "C" {
 
 qsim_status qsim_batch_destroy(qsim_batch *b) {
     if (!b) return QSIM_OK;
-    if (b->stream || true) cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->stream);
+    b->drop_graph();
     for (int i = 0; i < b->count; i++) {
         if (b->own[i]) cudaStreamSynchronize(b->own[i]);
         if (b->inst[i]) {
@@ -1095,6 +1110,7 @@ qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dty
 
 qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg) {
     if (!b || !cfg) return bfail(b, QSIM_E_INVAL, "null argument");
+    b->drop_graph();
     for (int i = 0; i < b->count; i++) {
         qsim_config c2 = *cfg;
         if (b->resident[i]) c2.tile_bits = b->inst[i]->n;  // residency is fixed at create
@@ -1106,6 +1122,7 @@ qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg) {
 
 qsim_status qsim_batch_set_seeds(qsim_batch *b, const uint64_t *seeds) {
     if (!b || !seeds) return bfail(b, QSIM_E_INVAL, "null argument");
+    b->drop_graph();
     for (int i = 0; i < b->count; i++) b->inst[i]->seed = seeds[i];
     return QSIM_OK;
 }
@@ -1117,6 +1134,7 @@ qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *g, siz
     if (ng && !g) return bfail(b, QSIM_E_INVAL, "gates is NULL");
     std::string err;
     if (!qsim::validate(c->n, g, ng, mats, nm, err)) return bfail(b, QSIM_E_INVAL, err);
+    b->drop_graph();
     release_instance_program(b, index);
     // programs live on the batch stream (aux): uploaded before, freed after, every run
     auto sink = [&](const Packed &pk) -> qsim_status {
@@ -1146,8 +1164,13 @@ qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *g, siz
     return QSIM_OK;
 }
 
-qsim_status qsim_batch_run(qsim_batch *b) {
-    if (!b) return fail(nullptr, QSIM_E_INVAL, "null batch");
+}  // extern "C"
+
+namespace {
+
+// Enqueue one run of every instance.  upload_table: (re)build and upload the
+// resident instances' table (eager runs); a captured run reuses the table.
+qsim_status enqueue_run(qsim_batch *b, bool upload_table) {
     qsim_ctx *c = b->aux;
     // resident instances, grouped by (width, largest op) so that each launch
     // sizes its shared memory for its own width
@@ -1186,7 +1209,7 @@ qsim_status qsim_batch_run(qsim_batch *b) {
         ic->ordinal = meas;
         ic->log_n = meas;
     }
-    if (!insts.empty()) {
+    if (!insts.empty() && upload_table) {
         if (insts.size() > b->insts_cap) {
             dfree(c, b->d_insts, b->insts_cap * sizeof(qsim::Instance));
             b->insts_cap = std::max(insts.size(), (size_t)64);
@@ -1198,6 +1221,8 @@ qsim_status qsim_batch_run(qsim_batch *b) {
         }
         qsim_status s = upload(c, b->d_insts, insts.data(), insts.size() * sizeof(qsim::Instance));
         if (s != QSIM_OK) return bfail(b, s, c->err);
+    }
+    if (!insts.empty()) {
         for (size_t gi = 0; gi < groups.size(); gi++) {
             const size_t first = groups[gi].second;
             const size_t last = gi + 1 < groups.size() ? groups[gi + 1].second : insts.size();
@@ -1216,6 +1241,46 @@ qsim_status qsim_batch_run(qsim_batch *b) {
         if (s == QSIM_OK) s = join_from(b, i);
         if (s != QSIM_OK) return bfail(b, s, ic->err);
     }
+    return QSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qsim_status qsim_batch_run(qsim_batch *b) {
+    if (!b) return fail(nullptr, QSIM_E_INVAL, "null batch");
+    qsim_ctx *c = b->aux;
+    if (b->graph_exec) {  // replay: one launch for every instance's whole circuit
+        CK(cudaGraphLaunch(b->graph_exec, b->stream), "batch graph launch");
+        for (int i = 0; i < b->count; i++) b->inst[i]->ordinal = b->inst[i]->log_n = b->meas_after[i];
+        return QSIM_OK;
+    }
+    if (b->eager_runs > 0) {  // capture the run (every allocation was made by the eager one)
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            qsim_status s = enqueue_run(b, false);
+            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            cudaGraphExec_t ge = nullptr;
+            if (s == QSIM_OK && e == cudaSuccess && g &&
+                cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+                b->graph = g;
+                b->graph_exec = ge;
+                CK(cudaGraphLaunch(b->graph_exec, b->stream), "batch graph launch");
+                return QSIM_OK;
+            }
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (s != QSIM_OK) return s;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    qsim_status s = enqueue_run(b, true);
+    if (s != QSIM_OK) return s;
+    b->eager_runs++;
+    b->meas_after.resize(b->count);
+    for (int i = 0; i < b->count; i++) b->meas_after[i] = b->inst[i]->log_n;
     return QSIM_OK;
 }
 

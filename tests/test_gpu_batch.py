@@ -64,6 +64,16 @@ def test_same_alone_and_in_the_mix(dtype):
     cs = mixed_circuits(seed=20)
     seeds = [7 + i for i in range(len(cs))]
     mix = run_batch(cs, dtype, dict(fusion=2), seeds)
+    # run 1 was eager, run 2 is captured into a CUDA graph, run 3 replays it:
+    # every run restarts from |0...0> and reproduces the same states and outcomes
+    first = [mix.state(i) for i in range(len(cs))]
+    first_out = [mix.outcomes(i)[0] for i in range(len(cs))]
+    for _ in range(2):
+        mix.run()
+        for i in range(len(cs)):
+            assert np.array_equal(mix.state(i), first[i]), i
+            out, _, st = mix.outcomes(i)
+            assert st == 0 and np.array_equal(out, first_out[i]), i
     for i in (0, 3, 5, 6):
         alone = run_batch([cs[i]], dtype, dict(fusion=2), [seeds[i]])
         assert np.array_equal(alone.state(0), mix.state(i)), i

@@ -259,8 +259,9 @@ QSIM_API const char *qsim_status_string(qsim_status s);
  * instances whose state fits one block's shared memory (n <= 14 for C64,
  * n <= 13 for C128, unless tile_bits forces tiling) run in ONE kernel launch,
  * one block per instance, with their measurements inside the kernel; larger
- * instances run their tile passes concurrently on per-instance streams that
- * fork from and join back to the batch stream.  Asynchronous.  The first run
+ * instances advance in lockstep, pass k of every one of them in a single
+ * multi-state tile launch (their measurements as launches between steps).
+ * Everything is enqueued on the batch stream.  Asynchronous.  The first run
  * after a compile, reconfiguration or reseeding is enqueued eagerly (and makes
  * every allocation); the second is captured into a CUDA graph that it and all
  * later runs launch with one call.  Each run restarts every state from

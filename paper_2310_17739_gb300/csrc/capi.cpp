@@ -956,10 +956,10 @@ qsim_status qsim_schedule(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng
 
 // ------------------------------------------------------------------ batches --
 // A batch is a set of ordinary contexts (one per instance: state, control
-// block, log) plus the launch plan: instances that fit one block's shared
-// memory run together in one resident launch per (width, op size) group on the
-// batch stream; the others run their tile passes on their own streams, forked
-// from and joined back to the batch stream.
+// block, log) plus the launch plan, all on the batch stream: instances that fit
+// one block's shared memory run together in one resident launch per (width,
+// op size) group; the others advance in lockstep, pass k of all of them in one
+// multi-state tile launch.
 struct qsim_batch {
     int count = 0;
     qsim_dtype dtype = QSIM_C64;
@@ -967,9 +967,6 @@ struct qsim_batch {
     std::vector<qsim_ctx *> inst;
     std::vector<std::vector<DevChunk>> prog;
     std::vector<char> resident;
-    std::vector<cudaStream_t> own;  // non-resident instances only
-    std::vector<cudaEvent_t> done;  // non-resident instances only
-    cudaEvent_t fork = nullptr;
     qsim_ctx *aux = nullptr;        // staging and scratch on the batch stream
     qsim::Instance *d_insts = nullptr;
     size_t insts_cap = 0;
@@ -978,11 +975,26 @@ struct qsim_batch {
     // run replay: after one eager run (which makes every allocation), the next
     // run is captured into a CUDA graph and later runs replay it with one launch;
     // compiling, reconfiguring or reseeding any instance drops the graph
+    // wide (tiled) instances advance in lockstep: step k runs pass k of every
+    // one of them in one multi-state launch (events as per-instance launches)
+    struct Step {
+        size_t first = 0;       // into tiled_descs
+        int count = 0;
+        uint32_t ctas = 0;
+        int max_m = 1, kmax = 1;
+        std::vector<std::pair<int, Pass>> events;  // (instance, event pass)
+    };
+    bool plan_valid = false;
+    std::vector<qsim::TileArgs> tiled_descs;
+    std::vector<Step> steps;
+    qsim::TileArgs *d_descs = nullptr;
+    size_t descs_cap = 0;
     int eager_runs = 0;
     std::vector<uint64_t> meas_after;  // log records per instance after one run
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     void drop_graph() {
+        plan_valid = false;
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         graph_exec = nullptr;
@@ -1014,21 +1026,6 @@ void release_instance_program(qsim_batch *b, int i) {
     b->prog[i].clear();
 }
 
-// fork: `s` waits for everything enqueued so far on the batch stream
-qsim_status fork_to(qsim_batch *b, cudaStream_t s) {
-    qsim_ctx *c = b->aux;
-    CK(cudaEventRecord(b->fork, b->stream), "fork event");
-    CK(cudaStreamWaitEvent(s, b->fork, 0), "fork wait");
-    return QSIM_OK;
-}
-
-qsim_status join_from(qsim_batch *b, int i) {
-    qsim_ctx *c = b->aux;
-    CK(cudaEventRecord(b->done[i], b->own[i]), "join event");
-    CK(cudaStreamWaitEvent(b->stream, b->done[i], 0), "join wait");
-    return QSIM_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -1038,19 +1035,16 @@ qsim_status qsim_batch_destroy(qsim_batch *b) {
     cudaStreamSynchronize(b->stream);
     b->drop_graph();
     for (int i = 0; i < b->count; i++) {
-        if (b->own[i]) cudaStreamSynchronize(b->own[i]);
         if (b->inst[i]) {
             release_instance_program(b, i);
             qsim_destroy(b->inst[i]);
         }
-        if (b->done[i]) cudaEventDestroy(b->done[i]);
-        if (b->own[i]) cudaStreamDestroy(b->own[i]);
     }
     if (b->aux) {
         dfree(b->aux, b->d_insts, b->insts_cap * sizeof(qsim::Instance));
+        dfree(b->aux, b->d_descs, b->descs_cap * sizeof(qsim::TileArgs));
         qsim_destroy(b->aux);
     }
-    if (b->fork) cudaEventDestroy(b->fork);
     if (b->h_init) cudaFreeHost(b->h_init);
     cudaGetLastError();
     delete b;
@@ -1071,12 +1065,9 @@ qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dty
     b->inst.assign(count, nullptr);
     b->prog.resize(count);
     b->resident.assign(count, 0);
-    b->own.assign(count, nullptr);
-    b->done.assign(count, nullptr);
     qsim_status s = qsim_create(1, dtype, stream, alloc, free_fn, user, &b->aux);
     if (s != QSIM_OK) return s;
-    if (cudaMallocHost((void **)&b->h_init, sizeof(MeasCtl)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaMallocHost((void **)&b->h_init, sizeof(MeasCtl)) != cudaSuccess) {
         cudaGetLastError();
         qsim_batch_destroy(b.release());
         return fail(nullptr, QSIM_E_OOM, "batch host resources");
@@ -1094,14 +1085,6 @@ qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dty
         if (n <= mx) {
             b->resident[i] = 1;
             b->inst[i]->cfg.tile_bits = n;  // the whole state in one block
-        } else {
-            if (cudaStreamCreateWithFlags(&b->own[i], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                qsim_batch_destroy(b.release());
-                return fail(nullptr, QSIM_E_CUDA, "instance stream");
-            }
-            b->inst[i]->stream = b->own[i];  // qsim_create synchronised its allocations
         }
     }
     *out = b.release();
@@ -1168,6 +1151,89 @@ qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *g, siz
 
 namespace {
 
+// Lockstep plan of the wide instances: step k holds pass k of each of them.
+// May only allocate/upload when `may_upload` (an eager run).
+qsim_status build_tiled_plan(qsim_batch *b, bool may_upload) {
+    qsim_ctx *c = b->aux;
+    b->tiled_descs.clear();
+    b->steps.clear();
+    for (int i = 0; i < b->count; i++) {
+        if (b->resident[i]) continue;
+        qsim_ctx *ic = b->inst[i];
+        size_t k = 0;
+        for (const DevChunk &dc : b->prog[i]) {
+            for (const Pass &p : dc.passes) {
+                if (!p.ev && !p.count) continue;
+                if (b->steps.size() <= k) b->steps.resize(k + 1);
+                auto &st = b->steps[k];
+                if (p.ev) {
+                    st.events.emplace_back(i, p);
+                } else {
+                    qsim::TileArgs a;
+                    if (!qsim::make_tile_args(b->dtype, ic->state, ic->n, dc.m, p.tile, dc.d_ops + p.first,
+                                              p.count, dc.d_mats, (uint32_t)p.mat_first, p.mat_count,
+                                              ic->ctl, &a))
+                        return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernel");
+                    a.pad = (uint32_t)std::max(dc.kmax, 1);  // op size, read back below
+                    b->tiled_descs.push_back(a);
+                    st.count++;
+                }
+                k++;
+            }
+        }
+    }
+    // group the descriptors by step (they were appended instance-major)
+    std::vector<qsim::TileArgs> by_step;
+    by_step.reserve(b->tiled_descs.size());
+    {
+        std::vector<std::vector<qsim::TileArgs>> per(b->steps.size());
+        size_t pos = 0;
+        for (int i = 0; i < b->count; i++) {
+            if (b->resident[i]) continue;
+            size_t k = 0;
+            for (const DevChunk &dc : b->prog[i])
+                for (const Pass &p : dc.passes) {
+                    if (!p.ev && !p.count) continue;
+                    if (!p.ev) per[k].push_back(b->tiled_descs[pos++]);
+                    k++;
+                }
+        }
+        for (size_t k = 0; k < per.size(); k++) {
+            auto &st = b->steps[k];
+            st.first = by_step.size();
+            st.count = (int)per[k].size();
+            uint32_t ctas = 0;
+            for (auto &a : per[k]) {
+                a.cta_first = ctas;
+                ctas += 1u << (a.n - a.m);
+                st.max_m = std::max(st.max_m, a.m);
+                st.kmax = std::max(st.kmax, (int)a.pad);
+                a.pad = 0;
+                by_step.push_back(a);
+            }
+            st.ctas = ctas;
+        }
+    }
+    b->tiled_descs.swap(by_step);
+    if (!b->tiled_descs.empty()) {
+        if (!may_upload) return bfail(b, QSIM_E_STATE, "batch plan changed during capture");
+        const size_t need = b->tiled_descs.size();
+        if (need > b->descs_cap) {
+            dfree(c, b->d_descs, b->descs_cap * sizeof(qsim::TileArgs));
+            b->descs_cap = need;
+            b->d_descs = (qsim::TileArgs *)dalloc(c, need * sizeof(qsim::TileArgs));
+            if (!b->d_descs) {
+                b->descs_cap = 0;
+                return bfail(b, QSIM_E_OOM, "multi-state pass table");
+            }
+        }
+        qsim_status s = upload(c, b->d_descs, b->tiled_descs.data(), need * sizeof(qsim::TileArgs));
+        if (s != QSIM_OK) return bfail(b, s, c->err);
+    }
+    b->plan_valid = true;
+    return QSIM_OK;
+}
+
 // Enqueue one run of every instance.  upload_table: (re)build and upload the
 // resident instances' table (eager runs); a captured run reuses the table.
 qsim_status enqueue_run(qsim_batch *b, bool upload_table) {
@@ -1231,15 +1297,28 @@ qsim_status enqueue_run(qsim_batch *b, bool upload_table) {
                "resident batch launch");
         }
     }
-    // tiled instances: concurrent on their own streams
+    // wide instances: lockstep steps, one multi-state launch per step
+    if (!b->plan_valid) {
+        qsim_status s = build_tiled_plan(b, upload_table);
+        if (s != QSIM_OK) return s;
+    }
     for (int i = 0; i < b->count; i++) {
         if (b->resident[i]) continue;
-        qsim_ctx *ic = b->inst[i];
-        qsim_status s = fork_to(b, b->own[i]);
-        if (s == QSIM_OK) s = reset_async(ic, b->h_init);
-        for (size_t k = 0; s == QSIM_OK && k < b->prog[i].size(); k++) s = launch_chunk(ic, b->prog[i][k]);
-        if (s == QSIM_OK) s = join_from(b, i);
-        if (s != QSIM_OK) return bfail(b, s, ic->err);
+        qsim_status s = reset_async(b->inst[i], b->h_init);
+        if (s != QSIM_OK) return bfail(b, s, b->inst[i]->err);
+    }
+    const int threads = b->dtype == QSIM_C64 && b->inst[0]->cfg.fusion == 2 ? 512 : 256;
+    for (const auto &st : b->steps) {
+        if (st.count)
+            CK(qsim::launch_tile_pass_multi(b->dtype, threads, st.kmax, b->d_descs + st.first, st.count,
+                                            st.ctas, st.max_m, b->stream),
+               "multi-state tile pass launch");
+        for (const auto &ev : st.events) {
+            qsim_ctx *ic = b->inst[ev.first];
+            qsim_status s = launch_measure(ic, (int)ev.second.q, ev.second.flags,
+                                           ev.second.ev == qsim::EV_RESET, ic->seed);
+            if (s != QSIM_OK) return bfail(b, s, ic->err);
+        }
     }
     return QSIM_OK;
 }
@@ -1325,14 +1404,12 @@ qsim_status qsim_batch_expect(qsim_batch *b, const qsim_pauli_term *terms, const
         if (b->resident[i] || off[i + 1] == off[i]) continue;
         qsim_ctx *ic = b->inst[i];
         const size_t nt = off[i + 1] - off[i];
-        s = fork_to(b, b->own[i]);
-        if (s == QSIM_OK) s = ensure_partials(ic, (size_t)qsim::expect_blocks(ic->n) * nt);
+        s = ensure_partials(ic, (size_t)qsim::expect_blocks(ic->n) * nt);
         if (s == QSIM_OK) {
             cudaError_t e = qsim::launch_expect(b->dtype, ic->state, ic->n, d_terms + 3 * off[i], nt,
-                                                ic->partials, d_out + off[i], ic->stream);
+                                                ic->partials, d_out + off[i], b->stream);
             if (e != cudaSuccess) s = cuda_fail(ic, e, "expectation launch");
         }
-        if (s == QSIM_OK) s = join_from(b, i);
     }
     if (s == QSIM_OK) {
         cudaError_t e = cudaMemcpyAsync(out, d_out, total * sizeof(double), cudaMemcpyDeviceToHost, b->stream);

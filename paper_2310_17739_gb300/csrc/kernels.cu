@@ -21,6 +21,7 @@
 #include "kernels.h"
 
 #include <cstdint>
+#include <cstring>
 
 namespace qsim {
 
@@ -368,27 +369,13 @@ __device__ __forceinline__ DevOp load_op(const DevOp *p) {
 // One pass: its op slice ops[0, n_ops) and coefficient slice (mat_count
 // complex values starting at element mat_first of the pool; op.mat is relative
 // to mat_first) are copied into shared memory together with the tile.
-struct TileArgs {
-    void *state;
-    const DevOp *ops;
-    const void *mats;
-    const MeasCtl *ctl;
-    uint32_t n_ops;
-    uint32_t mat_first;
-    uint32_t mat_count;
-    int n;
-    int m;
-    int L;
-    uint8_t tq[16];   // tile qubits, ascending (m entries)
-    uint8_t ntq[48];  // other qubits, ascending (n - m entries)
-};
 
 constexpr int kMaxHi = 1024;  // 2^(m - L) entries, m - L <= 10
 
 template <typename R, int NT, int KMAX>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a) {
+__device__ __forceinline__ void tile_pass_body(const TileArgs &a, const uint64_t bid,
+                                               unsigned char *smem_raw) {
     using T = typename V2<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
     T *mats_s = tile + (1u << a.m);                                   // kPassMats values
     DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);     // kPassOps ops
@@ -406,10 +393,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
     // 2. global offsets of the tile rows: non-tile bits from blockIdx, tile bits
     //    above the L contiguous low ones from the row index
     uint64_t base = 0;
-    {
-        const uint64_t bid = blockIdx.x;
-        for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << a.ntq[j];
-    }
+    for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << a.ntq[j];
     const int L = a.L, hib = a.m - L;
     for (int r = threadIdx.x; r < (1 << hib); r += NT) {
         uint64_t o = base;
@@ -449,6 +433,33 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
     } else {
         for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];
     }
+}
+
+template <typename R, int NT, int KMAX>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_pass_body<R, NT, KMAX>(a, blockIdx.x, smem_raw);
+}
+
+// One pass of several independent states in one launch: descs[j] covers
+// blocks [cta_first_j, cta_first_{j+1}); each block finds its state's pass by
+// binary search and runs it on tile (blockIdx.x - cta_first_j).
+template <typename R, int NT, int KMAX>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass_multi(const TileArgs *descs,
+                                                                            int n_desc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ TileArgs d;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_desc - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].cta_first <= blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        d = descs[lo];
+    }
+    __syncthreads();
+    tile_pass_body<R, NT, KMAX>(d, blockIdx.x - d.cta_first, smem_raw);
 }
 
 // -------------------------------------------------------------- resident --
@@ -746,6 +757,12 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 512, 2>));
     QSIM_ATTR((k_tile_pass<float, 256, 5>));
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
+    QSIM_ATTR((k_tile_pass_multi<float, 256, 2>));
+    QSIM_ATTR((k_tile_pass_multi<double, 256, 2>));
+    QSIM_ATTR((k_tile_pass_multi<float, 512, 2>));
+    QSIM_ATTR((k_tile_pass_multi<double, 512, 2>));
+    QSIM_ATTR((k_tile_pass_multi<float, 256, 5>));
+    QSIM_ATTR((k_tile_pass_multi<double, 256, 5>));
     QSIM_ATTR((k_resident_one<float, 256, 2>));
     QSIM_ATTR((k_resident_one<double, 256, 2>));
     QSIM_ATTR((k_resident_batch<float, 256, 2>));
@@ -758,13 +775,14 @@ cudaError_t setup_kernels() {
     return cudaSuccess;
 }
 
-cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
-                             uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
-                             uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
-                             cudaStream_t s) {
-    if (n_ops > (uint32_t)kPassOps || mat_count > (uint32_t)kPassMats || m > 15 || n - m > 48)
-        return cudaErrorInvalidValue;
-    TileArgs a;
+bool make_tile_args(int dtype, void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
+                    uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
+                    const MeasCtl *ctl, TileArgs *out) {
+    if (n_ops > (uint32_t)kPassOps || mat_count > (uint32_t)kPassMats || m > 15 || n - m > 48 ||
+        m < 1 || m > n)
+        return false;
+    TileArgs &a = *out;
+    std::memset(&a, 0, sizeof(a));
     a.state = state;
     a.ops = ops;
     a.mats = mats;
@@ -776,16 +794,30 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
     a.m = m;
     int t = 0, u = 0;
     for (int b = 0; b < n; b++) {
-        if ((tile_mask >> b) & 1ull) a.tq[t++] = (uint8_t)b;
-        else a.ntq[u++] = (uint8_t)b;
+        if ((tile_mask >> b) & 1ull) {
+            if (t >= 16) return false;
+            a.tq[t++] = (uint8_t)b;
+        } else {
+            a.ntq[u++] = (uint8_t)b;
+        }
     }
-    if (t != m) return cudaErrorInvalidValue;
+    if (t != m) return false;
     // contiguous low qubits of the tile (the coalesced run length), capped at
     // 128-byte runs; a pass may lack them when its first op needs the room
-    int low = __builtin_ctzll(~tile_mask);
+    const int low = __builtin_ctzll(~tile_mask);
     const int cap = dtype == 0 ? 4 : 3;
     a.L = low < cap ? low : cap;
     if (a.L > m) a.L = m;
+    return true;
+}
+
+cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
+                             uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
+                             uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
+                             cudaStream_t s) {
+    TileArgs a;
+    if (!make_tile_args(dtype, state, n, m, tile_mask, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
+        return cudaErrorInvalidValue;
     const unsigned grid = 1u << (n - m);
     const size_t smem = tile_smem_bytes(dtype, m);
     if (kmax > 2) {
@@ -797,6 +829,23 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
     } else {
         if (threads == 512) k_tile_pass<double, 512, 2><<<grid, 512, smem, s>>>(a);
         else k_tile_pass<double, 256, 2><<<grid, 256, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,
+                                   int n_desc, uint32_t total_ctas, int max_m, cudaStream_t s) {
+    if (n_desc <= 0 || total_ctas == 0) return cudaSuccess;
+    const size_t smem = tile_smem_bytes(dtype, max_m);
+    if (kmax > 2) {
+        if (dtype == 0) k_tile_pass_multi<float, 256, 5><<<total_ctas, 256, smem, s>>>(d_descs, n_desc);
+        else k_tile_pass_multi<double, 256, 5><<<total_ctas, 256, smem, s>>>(d_descs, n_desc);
+    } else if (dtype == 0) {
+        if (threads == 512) k_tile_pass_multi<float, 512, 2><<<total_ctas, 512, smem, s>>>(d_descs, n_desc);
+        else k_tile_pass_multi<float, 256, 2><<<total_ctas, 256, smem, s>>>(d_descs, n_desc);
+    } else {
+        if (threads == 512) k_tile_pass_multi<double, 512, 2><<<total_ctas, 512, smem, s>>>(d_descs, n_desc);
+        else k_tile_pass_multi<double, 256, 2><<<total_ctas, 256, smem, s>>>(d_descs, n_desc);
     }
     return cudaGetLastError();
 }

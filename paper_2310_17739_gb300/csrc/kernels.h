@@ -85,6 +85,34 @@ cudaError_t setup_kernels();
 size_t resident_smem_bytes(int dtype, int n);
 int max_resident_bits(int dtype);
 
+// One tile pass: its op slice ops[0, n_ops) and coefficient slice (mat_count
+// complex values starting at element mat_first of the pool; op.mat relative to
+// mat_first) are copied into shared memory together with the tile.
+struct TileArgs {
+    void *state;
+    const DevOp *ops;
+    const void *mats;
+    const MeasCtl *ctl;
+    uint32_t n_ops;
+    uint32_t mat_first;
+    uint32_t mat_count;
+    int n;
+    int m;
+    int L;
+    uint32_t cta_first;  // multi-state launches: first block of this state's pass
+    uint32_t pad;
+    uint8_t tq[16];      // tile qubits, ascending (m entries)
+    uint8_t ntq[48];     // other qubits, ascending (n - m entries)
+};
+// Fill a TileArgs for a pass over tile_mask (returns false if it cannot run).
+bool make_tile_args(int dtype, void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
+                    uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
+                    const MeasCtl *ctl, TileArgs *out);
+// Several states' passes in one launch: descs[0..n_desc) in device memory with
+// increasing cta_first; total_ctas blocks; max_m the largest tile among them.
+cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,
+                                   int n_desc, uint32_t total_ctas, int max_m, cudaStream_t s);
+
 // Per-pass limits of the tile kernel: the pass's ops and coefficients are
 // copied into shared memory next to the tile.
 constexpr int kPassOps = 256;

@@ -297,6 +297,49 @@ QSIM_API qsim_status qsim_batch_outcomes(qsim_batch *b, int index, int32_t *outc
 /* Number of instances run resident (one block each, one launch) by qsim_batch_run. */
 QSIM_API qsim_status qsim_batch_resident_count(const qsim_batch *b, int *count);
 
+/* ---------------------------------------------------------------- serving --
+ * A request loop with continuous admission.  qsim_server_submit copies a
+ * request (its gate records) into a pending queue and returns at once; host
+ * worker threads compile pending requests (fusion of Section "Gate Fusion",
+ * passes as for qsim_apply); a native scheduler thread admits compiled
+ * requests in arrival order whenever one of `slots` CUDA streams is idle and
+ * the request's device memory (state + program) fits the remaining budget,
+ * then enqueues the whole request on that slot's stream: state |0...0>, every
+ * pass and measurement (draws with the request's seed), <Z_q> of every qubit,
+ * and the read-back.  Requests on different slots overlap on the GPU; a
+ * request's state stays resident until its result is read back, then its
+ * memory returns to the budget and the next request is admitted.
+ * Results are delivered through qsim_server_poll in completion order.
+ * Times are host steady-clock seconds since the server was created. */
+typedef struct qsim_server qsim_server;
+typedef struct {
+    uint64_t id;              /* as returned by qsim_server_submit */
+    int32_t status;           /* QSIM_OK, QSIM_E_ZEROPROB, ... */
+    int32_t n_qubits;
+    int32_t n_meas;           /* MEASURE/RESET records in the request */
+    int32_t pad;
+    uint64_t outcomes;        /* bit i = outcome of the i-th of the first 64 measurements */
+    double success;           /* product of asserted P(0) (1 if none) */
+    double z[32];             /* <Z_q> for q < min(n, 32) */
+    double t_submit, t_admit, t_done;
+} qsim_result;
+/* slots: concurrent requests (1..64); mem_budget: device bytes for states and
+ * programs (0 = 80% of the free device memory at creation). */
+QSIM_API qsim_status qsim_server_create(int slots, size_t mem_budget, qsim_dtype dtype,
+                                        const qsim_config *cfg, int compile_threads,
+                                        qsim_server **out);
+QSIM_API qsim_status qsim_server_destroy(qsim_server *s);
+/* t_submit < 0: use the current time; else the request's arrival time (s). */
+QSIM_API qsim_status qsim_server_submit(qsim_server *s, int n_qubits, const qsim_gate *gates,
+                                        size_t n_gates, const double *mats, size_t n_mats,
+                                        uint64_t seed, double t_submit, uint64_t *id);
+/* Move up to cap finished results into out; *n_out = how many. */
+QSIM_API qsim_status qsim_server_poll(qsim_server *s, qsim_result *out, size_t cap, size_t *n_out);
+/* Counters: submitted, admitted, completed, pending (not yet admitted), running. */
+QSIM_API qsim_status qsim_server_counts(const qsim_server *s, uint64_t *submitted, uint64_t *admitted,
+                                        uint64_t *completed, uint64_t *pending, uint64_t *running);
+QSIM_API double qsim_server_now(const qsim_server *s);
+
 /* ------------------------------------------------ no-allocation variant --
  * The paper has no counterpart to this entry point; it serves callers that
  * own a state vector in device memory but may not allocate device memory

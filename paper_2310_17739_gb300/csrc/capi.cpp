@@ -3,7 +3,9 @@
 // (host threads compile chunks of the gate stream while earlier chunks run).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
+#include <deque>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -1441,6 +1443,419 @@ qsim_status qsim_batch_resident_count(const qsim_batch *b, int *count) {
     int k = 0;
     for (int i = 0; i < b->count; i++) k += b->resident[i];
     *count = k;
+    return QSIM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ serving --
+// Requests flow: submit (caller thread) -> pending -> compile workers -> ready
+// -> scheduler thread admits into an idle slot (stream) when the request's
+// device bytes fit the budget -> completion event -> result queue -> poll.
+namespace {
+
+struct ServerReq {
+    uint64_t id = 0;
+    int n = 0;
+    std::vector<qsim_gate> gates;
+    std::vector<double> mats;
+    uint64_t seed = 0;
+    double t_submit = 0, t_admit = 0;
+    std::vector<Packed> chunks;
+    size_t device_bytes = 0;
+    uint64_t n_meas = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    qsim_ctx *aux = nullptr;  // staging for uploads on this slot's stream
+    std::unique_ptr<ServerReq> req;
+    qsim_ctx *ctx = nullptr;  // the running request's state, control block, log
+    std::vector<DevChunk> prog;
+    // read-back (pinned) and the <Z_q> terms / outputs (device)
+    MeasCtl *h_ctl = nullptr;
+    MeasRec *h_log = nullptr;
+    double *h_z = nullptr;
+    uint64_t *d_terms = nullptr;
+    double *d_z = nullptr;
+};
+
+constexpr int kMaxLog = 64;
+
+double steady_now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// A request context created without synchronising: state |0...0> and a
+// cleared control block are enqueued on `st`; h_ctl is borrowed.
+qsim_ctx *ctx_new_async(int n, qsim_dtype dt, cudaStream_t st, const Config &cfg, MeasCtl *h_ctl,
+                        const MeasCtl *h_init) {
+    auto *c = new qsim_ctx();
+    c->n = n;
+    c->dtype = dt;
+    c->stream = st;
+    c->cfg = cfg;
+    cudaGetDevice(&c->device);
+    c->state_bytes = (size_t)(dt == QSIM_C64 ? 8 : 16) << n;
+    c->state = dalloc(c, c->state_bytes);
+    c->ctl = (MeasCtl *)dalloc(c, sizeof(MeasCtl));
+    c->h_ctl = h_ctl;
+    if (!c->state || !c->ctl || qsim::launch_set_basis(dt, c->state, n, 0, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->ctl, h_init, sizeof(MeasCtl), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        dfree(c, c->state, c->state_bytes);
+        dfree(c, c->ctl, sizeof(MeasCtl));
+        delete c;
+        return nullptr;
+    }
+    return c;
+}
+
+void ctx_free_async(qsim_ctx *c) {
+    dfree(c, c->state, c->state_bytes);
+    dfree(c, c->ctl, sizeof(MeasCtl));
+    dfree(c, c->log, c->log_cap * sizeof(MeasRec));
+    dfree(c, c->partials, c->partials_cap * sizeof(double));
+    for (auto &s : c->staging) {
+        cudaEventSynchronize(s.done);
+        cudaEventDestroy(s.done);
+        cudaFreeHost(s.host);
+    }
+    delete c;  // h_ctl is borrowed from the slot
+}
+
+}  // namespace
+
+struct qsim_server {
+    qsim_dtype dtype = QSIM_C64;
+    Config cfg;
+    int device = 0;
+    double t0 = 0;
+    size_t budget = 0, in_use = 0;
+    std::vector<Slot> slots;
+    MeasCtl *h_init = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_sched;
+    std::deque<std::unique_ptr<ServerReq>> pending;               // to compile
+    std::vector<std::unique_ptr<ServerReq>> ready;                // compiled, by id - first_ready_id
+    uint64_t next_id = 1, next_admit = 1;
+    std::vector<qsim_result> results;
+    std::atomic<uint64_t> submitted{0}, admitted{0}, completed{0}, running{0};
+    std::vector<std::thread> workers;
+    std::thread sched;
+    std::atomic<bool> stop{false};
+    std::string err;
+};
+
+namespace {
+
+void server_compile_loop(qsim_server *s) {
+    for (;;) {
+        std::unique_ptr<ServerReq> r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] { return s->stop.load() || !s->pending.empty(); });
+            if (s->stop.load()) return;
+            r = std::move(s->pending.front());
+            s->pending.pop_front();
+        }
+        Config c = s->cfg;
+        if (r->n <= qsim::max_resident_bits(s->dtype)) c.tile_bits = r->n;  // one block per request
+        HostProgram hp;
+        qsim::compile(r->n, s->dtype, c, r->gates.data(), r->gates.size(), r->mats.data(), r->mats.size(), hp);
+        Packed pk;
+        pack(hp, s->dtype, pk);
+        r->n_meas = pk.measurements;
+        r->device_bytes = ((size_t)(s->dtype == QSIM_C64 ? 8 : 16) << r->n) + pk.ops.size() * sizeof(DevOp) +
+                          pk.mats.size() + (size_t)std::max<uint64_t>(r->n_meas, 1024) * sizeof(MeasRec) +
+                          (size_t)qsim::expect_blocks(r->n) * 32 * sizeof(double) + 4096;
+        r->chunks.push_back(std::move(pk));
+        std::vector<qsim_gate>().swap(r->gates);  // the compiled program replaces the records
+        std::vector<double>().swap(r->mats);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            const uint64_t idx = r->id - s->next_admit;  // ready[k] holds id next_admit + k
+            if (s->ready.size() <= idx) s->ready.resize(idx + 1);
+            s->ready[idx] = std::move(r);
+        }
+        s->cv_sched.notify_all();
+    }
+}
+
+void server_finish(qsim_server *s, Slot &sl) {
+    ServerReq &r = *sl.req;
+    qsim_result res;
+    std::memset(&res, 0, sizeof(res));
+    res.id = r.id;
+    res.n_qubits = r.n;
+    res.n_meas = (int32_t)r.n_meas;
+    res.status = sl.h_ctl->status;
+    res.success = sl.h_ctl->success;
+    const int nl = (int)std::min<uint64_t>(r.n_meas, kMaxLog);
+    for (int i = 0; i < nl; i++)
+        if (sl.h_log[i].outcome == 1) res.outcomes |= 1ull << i;
+    const int nz = std::min(r.n, 32);
+    for (int q = 0; q < nz; q++) res.z[q] = sl.h_z[q];
+    res.t_submit = r.t_submit;
+    res.t_admit = r.t_admit;
+    res.t_done = steady_now() - s->t0;
+    for (auto &dc : sl.prog) release_chunk(sl.aux, dc);
+    sl.prog.clear();
+    ctx_free_async(sl.ctx);
+    sl.ctx = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->in_use -= r.device_bytes;
+        s->results.push_back(res);
+    }
+    sl.req.reset();
+    s->running--;
+    s->completed++;
+}
+
+// Enqueue a whole request on an idle slot.  Returns false (with an error
+// result delivered) if it could not be enqueued.
+bool server_admit(qsim_server *s, Slot &sl, std::unique_ptr<ServerReq> r) {
+    r->t_admit = steady_now() - s->t0;
+    Config c = s->cfg;
+    if (r->n <= qsim::max_resident_bits(s->dtype)) c.tile_bits = r->n;
+    qsim_ctx *ctx = ctx_new_async(r->n, s->dtype, sl.stream, c, sl.h_ctl, s->h_init);
+    qsim_status st = ctx ? QSIM_OK : QSIM_E_OOM;
+    if (ctx) ctx->seed = r->seed;
+    for (auto &pk : r->chunks) {
+        if (st != QSIM_OK) break;
+        DevChunk dc;
+        st = upload_chunk(sl.aux, pk, dc);
+        sl.prog.push_back(std::move(dc));
+    }
+    for (auto &dc : sl.prog) {
+        if (st != QSIM_OK) break;
+        st = launch_chunk(ctx, dc);
+    }
+    const int nz = std::min(r->n, 32);
+    if (st == QSIM_OK) st = ensure_partials(ctx, (size_t)qsim::expect_blocks(r->n) * nz);
+    if (st == QSIM_OK && qsim::launch_expect(s->dtype, ctx->state, r->n, sl.d_terms, nz, ctx->partials,
+                                             sl.d_z, sl.stream) != cudaSuccess)
+        st = QSIM_E_CUDA;
+    if (st == QSIM_OK) {
+        const int nl = (int)std::min<uint64_t>(r->n_meas, kMaxLog);
+        cudaError_t e = cudaMemcpyAsync(sl.h_ctl, ctx->ctl, sizeof(MeasCtl), cudaMemcpyDeviceToHost, sl.stream);
+        if (e == cudaSuccess && nl)
+            e = cudaMemcpyAsync(sl.h_log, ctx->log, nl * sizeof(MeasRec), cudaMemcpyDeviceToHost, sl.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.h_z, sl.d_z, nz * sizeof(double), cudaMemcpyDeviceToHost, sl.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+        if (e != cudaSuccess) st = QSIM_E_CUDA;
+    }
+    for (auto &pk : r->chunks) pk = Packed();  // host image no longer needed
+    if (st != QSIM_OK) {
+        cudaGetLastError();
+        cudaStreamSynchronize(sl.stream);
+        for (auto &dc : sl.prog) release_chunk(sl.aux, dc);
+        sl.prog.clear();
+        if (ctx) ctx_free_async(ctx);
+        qsim_result res;
+        std::memset(&res, 0, sizeof(res));
+        res.id = r->id;
+        res.n_qubits = r->n;
+        res.status = st;
+        res.t_submit = r->t_submit;
+        res.t_admit = r->t_admit;
+        res.t_done = steady_now() - s->t0;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->in_use -= r->device_bytes;
+        s->results.push_back(res);
+        s->completed++;
+        return false;
+    }
+    sl.ctx = ctx;
+    sl.req = std::move(r);
+    s->running++;
+    s->admitted++;
+    return true;
+}
+
+void server_sched_loop(qsim_server *s) {
+    cudaSetDevice(s->device);
+    while (!s->stop.load()) {
+        bool progress = false;
+        for (auto &sl : s->slots)
+            if (sl.req && cudaEventQuery(sl.done) == cudaSuccess) {
+                server_finish(s, sl);
+                progress = true;
+            }
+        cudaGetLastError();  // cudaErrorNotReady from the queries
+        for (auto &sl : s->slots) {
+            if (sl.req) continue;
+            std::unique_ptr<ServerReq> r;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (s->ready.empty() || !s->ready.front()) break;  // strict arrival order
+                const size_t need = s->ready.front()->device_bytes;
+                const bool alone = s->running.load() == 0;
+                if (need > s->budget - s->in_use && !alone) break;  // wait for memory to free up
+                r = std::move(s->ready.front());
+                s->ready.erase(s->ready.begin());
+                s->next_admit++;
+                s->in_use += r->device_bytes;
+            }
+            server_admit(s, sl, std::move(r));
+            progress = true;
+        }
+        if (!progress) {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_sched.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+qsim_status qsim_server_destroy(qsim_server *s) {
+    if (!s) return QSIM_OK;
+    s->stop = true;
+    s->cv_work.notify_all();
+    s->cv_sched.notify_all();
+    for (auto &t : s->workers)
+        if (t.joinable()) t.join();
+    if (s->sched.joinable()) s->sched.join();
+    cudaSetDevice(s->device);
+    for (auto &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.req) {
+            for (auto &dc : sl.prog) release_chunk(sl.aux, dc);
+            if (sl.ctx) ctx_free_async(sl.ctx);
+        }
+        if (sl.aux) {
+            dfree(sl.aux, sl.d_terms, 32 * 3 * sizeof(uint64_t));
+            dfree(sl.aux, sl.d_z, 32 * sizeof(double));
+            qsim_destroy(sl.aux);
+        }
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.h_ctl) cudaFreeHost(sl.h_ctl);
+        if (sl.h_log) cudaFreeHost(sl.h_log);
+        if (sl.h_z) cudaFreeHost(sl.h_z);
+    }
+    if (s->h_init) cudaFreeHost(s->h_init);
+    cudaGetLastError();
+    delete s;
+    return QSIM_OK;
+}
+
+qsim_status qsim_server_create(int slots, size_t mem_budget, qsim_dtype dtype, const qsim_config *cfg,
+                               int compile_threads, qsim_server **out) {
+    if (!out) return fail(nullptr, QSIM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (slots < 1 || slots > 64) return fail(nullptr, QSIM_E_INVAL, "slots must be in [1, 64]");
+    if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(nullptr, QSIM_E_INVAL, "bad dtype");
+    auto s = std::make_unique<qsim_server>();
+    s->dtype = dtype;
+    s->cfg = qsim::config_from(cfg);
+    s->t0 = steady_now();
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, QSIM_E_CUDA, "no CUDA device");
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, QSIM_E_CUDA, "cudaMemGetInfo");
+    }
+    s->budget = mem_budget ? mem_budget : (size_t)(0.8 * (double)free_b);
+    if (cudaMallocHost((void **)&s->h_init, sizeof(MeasCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, QSIM_E_OOM, "pinned memory");
+    }
+    std::memset(s->h_init, 0, sizeof(MeasCtl));
+    s->h_init->success = 1.0;
+    // <Z_q> terms for q < 32, shared layout with qsim_pauli_term
+    std::vector<uint64_t> zt(32 * 3, 0);
+    const double one = 1.0;
+    for (int q = 0; q < 32; q++) {
+        zt[3 * q + 1] = 1ull << q;
+        std::memcpy(&zt[3 * q + 2], &one, sizeof(one));
+    }
+    s->slots.resize(slots);
+    for (auto &sl : s->slots) {
+        bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaMallocHost((void **)&sl.h_ctl, sizeof(MeasCtl)) == cudaSuccess &&
+                  cudaMallocHost((void **)&sl.h_log, kMaxLog * sizeof(MeasRec)) == cudaSuccess &&
+                  cudaMallocHost((void **)&sl.h_z, 32 * sizeof(double)) == cudaSuccess;
+        if (ok) ok = qsim_create(1, dtype, sl.stream, nullptr, nullptr, nullptr, &sl.aux) == QSIM_OK;
+        if (ok) {
+            sl.d_terms = (uint64_t *)dalloc(sl.aux, zt.size() * sizeof(uint64_t));
+            sl.d_z = (double *)dalloc(sl.aux, 32 * sizeof(double));
+            ok = sl.d_terms && sl.d_z && upload(sl.aux, sl.d_terms, zt.data(), zt.size() * sizeof(uint64_t)) == QSIM_OK &&
+                 cudaStreamSynchronize(sl.stream) == cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            qsim_server_destroy(s.release());
+            return fail(nullptr, QSIM_E_CUDA, "server slot set-up failed");
+        }
+    }
+    int T = compile_threads > 0 ? compile_threads
+                                : (int)std::max(1u, std::min(std::thread::hardware_concurrency() / 2, 16u));
+    qsim_server *raw = s.get();
+    for (int t = 0; t < T; t++) s->workers.emplace_back(server_compile_loop, raw);
+    s->sched = std::thread(server_sched_loop, raw);
+    *out = s.release();
+    return QSIM_OK;
+}
+
+double qsim_server_now(const qsim_server *s) { return s ? steady_now() - s->t0 : 0.0; }
+
+qsim_status qsim_server_submit(qsim_server *s, int n, const qsim_gate *g, size_t ng, const double *mats,
+                               size_t nm, uint64_t seed, double t_submit, uint64_t *id) {
+    if (!s) return fail(nullptr, QSIM_E_INVAL, "null server");
+    if (n < 1 || n > 34) return fail(nullptr, QSIM_E_INVAL, "n_qubits must be in [1, 34]");
+    if (ng && !g) return fail(nullptr, QSIM_E_INVAL, "gates is NULL");
+    std::string err;
+    if (!qsim::validate(n, g, ng, mats, nm, err)) return fail(nullptr, QSIM_E_INVAL, err);
+    auto r = std::make_unique<ServerReq>();
+    r->n = n;
+    r->gates.assign(g, g + ng);
+    if (mats && nm) r->mats.assign(mats, mats + nm);
+    r->seed = seed;
+    r->t_submit = t_submit >= 0 ? t_submit : steady_now() - s->t0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->id = s->next_id++;
+        if (id) *id = r->id;
+        s->pending.push_back(std::move(r));
+    }
+    s->submitted++;
+    s->cv_work.notify_one();
+    return QSIM_OK;
+}
+
+qsim_status qsim_server_poll(qsim_server *s, qsim_result *out, size_t cap, size_t *n_out) {
+    if (!s) return fail(nullptr, QSIM_E_INVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t k = std::min(cap, s->results.size());
+    if (k) {
+        std::memcpy(out, s->results.data(), k * sizeof(qsim_result));
+        s->results.erase(s->results.begin(), s->results.begin() + k);
+    }
+    if (n_out) *n_out = k;
+    return QSIM_OK;
+}
+
+qsim_status qsim_server_counts(const qsim_server *s, uint64_t *submitted, uint64_t *admitted,
+                               uint64_t *completed, uint64_t *pending, uint64_t *running) {
+    if (!s) return QSIM_E_INVAL;
+    const uint64_t sub = s->submitted.load(), adm = s->admitted.load(), done = s->completed.load();
+    if (submitted) *submitted = sub;
+    if (admitted) *admitted = adm;
+    if (completed) *completed = done;
+    if (running) *running = s->running.load();
+    if (pending) *pending = sub >= adm ? sub - adm : 0;
     return QSIM_OK;
 }
 

@@ -45,6 +45,13 @@ class ProgramInfo(ctypes.Structure):
                 ("op_hist", ctypes.c_uint64 * 8)]
 
 
+class QsimResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_qubits", ctypes.c_int32),
+                ("n_meas", ctypes.c_int32), ("pad", ctypes.c_int32), ("outcomes", ctypes.c_uint64),
+                ("success", ctypes.c_double), ("z", ctypes.c_double * 32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -81,6 +88,13 @@ _SIGS = {
     "qsim_batch_state": ([_vp, _i32, _vp, _sz, _i32], _i32),
     "qsim_batch_outcomes": ([_vp, _i32, _vp, _vp, _sz, ctypes.POINTER(_sz)], _i32),
     "qsim_batch_resident_count": ([_vp, ctypes.POINTER(_i32)], _i32),
+    "qsim_server_create": ([_i32, _sz, _i32, ctypes.POINTER(QsimConfig), _i32, ctypes.POINTER(_vp)], _i32),
+    "qsim_server_destroy": ([_vp], _i32),
+    "qsim_server_submit": ([_vp, _i32, _vp, _sz, _vp, _sz, _u64, _dbl, ctypes.POINTER(_u64)], _i32),
+    "qsim_server_poll": ([_vp, _vp, _sz, ctypes.POINTER(_sz)], _i32),
+    "qsim_server_counts": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                            ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i32),
+    "qsim_server_now": ([_vp], _dbl),
     "qsim_profile_start": ([_vp, _i32], _i32),
     "qsim_profile_read": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_u64), ctypes.POINTER(_dbl),
                            ctypes.POINTER(_dbl), ctypes.POINTER(_u64)], _i32),
@@ -402,6 +416,65 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             _lib.qsim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-admission request loop (see qsim_server_* in qsim.h)."""
+
+    def __init__(self, slots: int = 16, mem_budget: int = 0, dtype: str = "c64",
+                 config: Optional[dict] = None, compile_threads: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        torch.cuda.current_device()
+        self.dtype = C64 if dtype in ("c64", C64) else C128
+        cfg = make_config(**(config or {}))
+        h = ctypes.c_void_p()
+        _check(_lib.qsim_server_create(slots, mem_budget, self.dtype, ctypes.byref(cfg), compile_threads,
+                                       ctypes.byref(h)))
+        self.h = h
+        self._buf = (QsimResult * 256)()
+
+    def submit(self, n: int, gates, mats=None, seed: int = 0, t_submit: float = -1.0) -> int:
+        g = _gates(gates)
+        m = _mats(mats)
+        rid = ctypes.c_uint64()
+        _check(_lib.qsim_server_submit(self.h, n, _ptr(g), g.size, _ptr(m), m.size, seed, t_submit,
+                                       ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self):
+        out = []
+        while True:
+            k = ctypes.c_size_t()
+            _check(_lib.qsim_server_poll(self.h, ctypes.cast(self._buf, ctypes.c_void_p), 256, ctypes.byref(k)))
+            for i in range(k.value):
+                r = self._buf[i]
+                out.append(dict(id=r.id, status=r.status, n=r.n_qubits, n_meas=r.n_meas,
+                                outcomes=r.outcomes, success=r.success,
+                                z=np.array(r.z[: min(r.n_qubits, 32)]), t_submit=r.t_submit,
+                                t_admit=r.t_admit, t_done=r.t_done))
+            if k.value < 256:
+                return out
+
+    def counts(self) -> dict:
+        v = [ctypes.c_uint64() for _ in range(5)]
+        _check(_lib.qsim_server_counts(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("submitted", "admitted", "completed", "pending", "running"), (x.value for x in v)))
+
+    def now(self) -> float:
+        return _lib.qsim_server_now(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qsim_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

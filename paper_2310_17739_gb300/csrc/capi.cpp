@@ -64,7 +64,6 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
     pk.gates = hp.gates;
     pk.measurements = hp.measurements;
     std::memcpy(pk.hist, hp.hist, sizeof(pk.hist));
-    pk.ops.resize(hp.ops.size());
     const size_t es = dt == QSIM_C64 ? 8 : 16;
     pk.mats.resize(hp.pool.size() * es);
     if (dt == QSIM_C64) {
@@ -76,45 +75,106 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
     } else if (!hp.pool.empty()) {
         std::memcpy(pk.mats.data(), hp.pool.data(), hp.pool.size() * 16);
     }
-    pk.passes = hp.passes;
+    // Ops are re-emitted pass by pass; a complex64 pass made only of rotations
+    // whose X masks have <= 5 tile qubits is laid out in register segments
+    // (a kSegMarker op, then its rotations) for the register tile kernel.
+    pk.passes.clear();
+    pk.ops.clear();
+    pk.ops.reserve(hp.ops.size() + hp.passes.size() * 2);
     uint64_t fused = 0, dp = 0;
-    for (const Pass &p : hp.passes) {
-        if (p.ev) {
-            const qsim::FOp &o = hp.ops[p.first];
-            DevOp &d = pk.ops[p.first];
+    const bool reg_dtype = dt == QSIM_C64 && !hp.resident && hp.m >= 10 && hp.m <= 14;
+    for (const Pass &src : hp.passes) {
+        Pass p = src;
+        p.first = pk.ops.size();
+        if (src.ev) {
+            const qsim::FOp &o = hp.ops[src.first];
+            DevOp d;
             std::memset(&d, 0, sizeof(d));
             d.ev = o.ev;
             d.flags = o.flags;
             d.lq[0] = (uint8_t)o.q[0];
+            pk.ops.push_back(d);
+            p.count = 1;
+            pk.passes.push_back(p);
             continue;
         }
         dp++;
-        for (uint64_t i = p.first; i < p.first + p.count; i++) {
+        auto local = [&](uint64_t q) {
+            return (uint32_t)__builtin_popcountll(src.tile & ((1ull << q) - 1ull));
+        };
+        auto to_local = [&](uint64_t mask) {
+            uint32_t l = 0;
+            for (int q = 0; q < 64; q++)
+                if ((mask >> q) & 1) l |= 1u << local(q);
+            return l;
+        };
+        std::vector<DevOp> body;
+        body.reserve(src.count);
+        bool all_rot = true;
+        for (uint64_t i = src.first; i < src.first + src.count; i++) {
             const qsim::FOp &o = hp.ops[i];
-            DevOp &d = pk.ops[i];
+            DevOp d;
             std::memset(&d, 0, sizeof(d));
             d.k = o.k;
-            auto local = [&](uint64_t q) {
-                return (uint32_t)__builtin_popcountll(p.tile & ((1ull << q) - 1ull));
-            };
             if (o.pauli()) {  // tile-local X and Z masks (<= 15 bits each) in lq[0..3]
-                uint32_t lx = 0, lz = 0;
-                for (int q = 0; q < 64; q++) {
-                    if ((o.xm >> q) & 1) lx |= 1u << local(q);
-                    if ((o.zm >> q) & 1) lz |= 1u << local(q);
-                }
+                const uint32_t lx = to_local(o.xm), lz = to_local(o.zm);
                 d.lq[0] = (uint8_t)(lx & 0xff);
                 d.lq[1] = (uint8_t)(lx >> 8);
                 d.lq[2] = (uint8_t)(lz & 0xff);
                 d.lq[3] = (uint8_t)(lz >> 8);
+                if (__builtin_popcount(lx) > 5) all_rot = false;
             } else {
                 for (int j = 0; j < o.k; j++) d.lq[j] = (uint8_t)local(o.q[j]);
+                all_rot = false;
             }
             // the tile kernel indexes the pass's own coefficient slice; the
             // resident kernel walks the whole pool
-            d.mat = (uint32_t)(hp.resident ? o.mat : o.mat - p.mat_first);
+            d.mat = (uint32_t)(hp.resident ? o.mat : o.mat - src.mat_first);
+            body.push_back(d);
             fused++;
         }
+        if (reg_dtype && all_rot) {
+            // greedy segments: grow the register set with each rotation's X
+            // positions while it stays <= 5; fill it up with the highest free
+            // positions (so that the lowest tile positions index threads)
+            std::vector<std::pair<uint32_t, std::vector<DevOp>>> segs;
+            uint32_t R = 0;
+            std::vector<DevOp> cur;
+            auto close = [&]() {
+                if (cur.empty()) return;
+                for (int b = src.tile ? __builtin_popcountll(src.tile) - 1 : 0; b >= 0 && __builtin_popcount(R) < 5; b--)
+                    R |= 1u << b;
+                segs.emplace_back(R, cur);
+                cur.clear();
+                R = 0;
+            };
+            for (const DevOp &d : body) {
+                const uint32_t x = d.lq[0] | ((uint32_t)d.lq[1] << 8);
+                if ((x & ~R) && __builtin_popcount(R | x) > 5) close();
+                R |= x;
+                cur.push_back(d);
+            }
+            close();
+            if (body.size() + segs.size() <= (size_t)qsim::kPassOps) {
+                for (auto &sg : segs) {
+                    DevOp m;
+                    std::memset(&m, 0, sizeof(m));
+                    m.k = qsim::kSegMarker;
+                    m.flags = (uint16_t)sg.second.size();
+                    for (int b = 0, j = 0; b < 32; b++)
+                        if ((sg.first >> b) & 1) m.lq[j++] = (uint8_t)b;
+                    pk.ops.push_back(m);
+                    pk.ops.insert(pk.ops.end(), sg.second.begin(), sg.second.end());
+                }
+                p.reg = 1;
+                p.count = (uint32_t)(pk.ops.size() - p.first);
+                pk.passes.push_back(p);
+                continue;
+            }
+        }
+        pk.ops.insert(pk.ops.end(), body.begin(), body.end());
+        p.count = (uint32_t)(pk.ops.size() - p.first);
+        pk.passes.push_back(p);
     }
     pk.fused = fused;
     pk.dense_passes = dp;
@@ -388,10 +448,15 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
         const bool sample = c->prof_every > 0 && c->prof_launches % (uint64_t)c->prof_every == 0 &&
                             c->prof_used < c->prof_ev.size();
         if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
-        CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile,
-                                  dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
-                                  p.mat_count, c->ctl, c->stream),
-           "tile pass launch");
+        if (p.reg && c->cfg.threads == 0)
+            CK(qsim::launch_tile_pass_reg(c->state, c->n, dc.m, p.tile, dc.d_ops + p.first, p.count, dc.d_mats,
+                                          (uint32_t)p.mat_first, p.mat_count, c->ctl, c->stream),
+               "register tile pass launch");
+        else
+            CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile,
+                                      dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
+                                      p.mat_count, c->ctl, c->stream),
+               "tile pass launch");
         if (sample) {
             CK(cudaEventRecord(c->prof_ev[c->prof_used].second, c->stream), "profile event");
             c->prof_used++;

@@ -60,7 +60,7 @@ struct Pass {
     uint64_t first = 0;
     uint32_t count = 0;
     uint8_t ev = EV_NONE;
-    uint8_t pad = 0;
+    uint8_t reg = 0;      // laid out in register segments (set when packed for the device)
     uint16_t flags = 0;   // event flags (bit 0: assertion mode)
     uint32_t q = 0;       // event qubit
     uint32_t fpa = 0;     // algorithmic real flops per amplitude of the pass (8 * 2^k per op)

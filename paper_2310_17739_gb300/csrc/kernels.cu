@@ -441,6 +441,165 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
     tile_pass_body<R, NT, KMAX>(a, blockIdx.x, smem_raw);
 }
 
+// ------------------------------------------------------ register segments --
+// complex64 rotation passes: each thread holds 32 amplitudes of the tile in
+// registers.  The pass is a list of segments (a kSegMarker op naming 5 tile
+// positions -- the "register qubits" -- followed by rotations whose X mask
+// lies within them); a rotation is then a butterfly between register slots s
+// and s ^ xr of one thread, with no shared-memory traffic and no barrier.
+// Shared memory is touched only to lay the tile out again between segments.
+constexpr int kRegAmps = 32;
+
+// a'_s = c a_s + (-1)^{par(s^xr)} sin * i^e a_{s^xr}, for both slots of each pair.
+// (sA, sB, sC, sD) = sin * (the 2x2 real form of multiplication by i^e).
+template <int XR>
+__device__ __forceinline__ void pauli_reg_pairs(float2 *a, float c, float sA, float sB, float sC,
+                                                float sD, unsigned zr, unsigned pt) {
+#pragma unroll
+    for (int s = 0; s < kRegAmps; s++) {
+        const int q = s ^ XR;
+        if (s < q) {
+            const float fs = ((__popc((unsigned)s & zr) ^ pt) & 1u) ? -1.f : 1.f;
+            const float fq = ((__popc((unsigned)q & zr) ^ pt) & 1u) ? -1.f : 1.f;
+            const float2 as = a[s], aq = a[q];
+            float2 ns, nq;
+            ns.x = c * as.x + fq * (sA * aq.x + sB * aq.y);
+            ns.y = c * as.y + fq * (sC * aq.x + sD * aq.y);
+            nq.x = c * aq.x + fs * (sA * as.x + sB * as.y);
+            nq.y = c * aq.y + fs * (sC * as.x + sD * as.y);
+            a[s] = ns;
+            a[q] = nq;
+        }
+    }
+}
+
+__device__ __forceinline__ void pauli_reg_diag(float2 *a, float c, float sn, unsigned zr, unsigned pt) {
+#pragma unroll
+    for (int s = 0; s < kRegAmps; s++) {
+        const float sg = ((__popc((unsigned)s & zr) ^ pt) & 1u) ? -sn : sn;
+        const float2 v = a[s];
+        a[s].x = c * v.x + sg * v.y;  // (c - i sg)(x + i y)
+        a[s].y = c * v.y - sg * v.x;
+    }
+}
+
+__device__ __forceinline__ void pauli_reg_dispatch(float2 *a, unsigned xr, float c, float sA, float sB,
+                                                float sC, float sD, unsigned zr, unsigned pt) {
+    switch (xr) {
+#define QSIM_XR(v) case v: pauli_reg_pairs<v>(a, c, sA, sB, sC, sD, zr, pt); break;
+        QSIM_XR(1) QSIM_XR(2) QSIM_XR(3) QSIM_XR(4) QSIM_XR(5) QSIM_XR(6) QSIM_XR(7) QSIM_XR(8)
+        QSIM_XR(9) QSIM_XR(10) QSIM_XR(11) QSIM_XR(12) QSIM_XR(13) QSIM_XR(14) QSIM_XR(15)
+        QSIM_XR(16) QSIM_XR(17) QSIM_XR(18) QSIM_XR(19) QSIM_XR(20) QSIM_XR(21) QSIM_XR(22)
+        QSIM_XR(23) QSIM_XR(24) QSIM_XR(25) QSIM_XR(26) QSIM_XR(27) QSIM_XR(28) QSIM_XR(29)
+        QSIM_XR(30) QSIM_XR(31)
+#undef QSIM_XR
+        default: break;
+    }
+}
+
+// Register-segment pass body (complex64, blockDim = 2^(m-5) threads).
+__device__ __forceinline__ void tile_pass_body_reg(const TileArgs &a, const uint64_t bid,
+                                                   unsigned char *smem_raw) {
+    using T = float2;
+    const unsigned NT = blockDim.x;
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    T *mats_s = tile + (1u << a.m);
+    DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);
+    __shared__ uint64_t hi_off[kMaxHi];
+    __shared__ unsigned roff[kRegAmps];
+    const int status = a.ctl->status;
+    for (unsigned i = threadIdx.x; i < a.n_ops; i += NT) cp_async16(ops_s + i, a.ops + i);
+    {
+        const T *gm = reinterpret_cast<const T *>(a.mats) + a.mat_first;
+        for (unsigned i = threadIdx.x; i < a.mat_count; i += NT) cp_async8(mats_s + i, gm + i);
+    }
+    uint64_t base = 0;
+    for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << a.ntq[j];
+    const int L = a.L, hib = a.m - L;
+    for (int r = threadIdx.x; r < (1 << hib); r += NT) {
+        uint64_t o = base;
+        for (int j = 0; j < hib; j++) o |= ((uint64_t)((r >> j) & 1)) << a.tq[L + j];
+        hi_off[r] = o;
+    }
+    __syncthreads();
+    T *st = reinterpret_cast<T *>(a.state);
+    const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
+    const bool vec = L >= 1;
+    if (vec) {
+        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
+            const unsigned l = p * 2;
+            cp_async16(tile + l, st + (hi_off[l >> L] | (l & Lmask)));
+        }
+    } else {
+        for (unsigned l = threadIdx.x; l < Nt; l += NT) cp_async8(tile + l, st + (hi_off[l >> L] | (l & Lmask)));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (status) return;
+    T reg[kRegAmps];
+    uint32_t i = 0;
+    while (i < a.n_ops) {
+        const DevOp seg = ops_s[i];  // kSegMarker: lq[0..4] register positions, flags = #ops
+        const unsigned nseg = seg.flags;
+        unsigned rmask = 0;
+#pragma unroll
+        for (int j = 0; j < 5; j++) rmask |= 1u << seg.lq[j];
+        // this thread's tile index on the non-register positions
+        unsigned tb = 0;
+        for (int b = 0, j = 0; b < a.m; b++)
+            if (!((rmask >> b) & 1u)) tb |= ((threadIdx.x >> j++) & 1u) << b;
+        if (threadIdx.x < kRegAmps) {
+            unsigned o = 0;
+#pragma unroll
+            for (int j = 0; j < 5; j++) o |= ((threadIdx.x >> j) & 1u) << seg.lq[j];
+            roff[threadIdx.x] = o;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < kRegAmps; s++) reg[s] = tile[tb | roff[s]];
+        for (uint32_t k = 1; k <= nseg; k++) {
+            const DevOp op = ops_s[i + k];
+            const unsigned x = op.lq[0] | ((unsigned)op.lq[1] << 8);
+            const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
+            unsigned xr = 0, zr = 0;
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                xr |= ((x >> seg.lq[j]) & 1u) << j;
+                zr |= ((z >> seg.lq[j]) & 1u) << j;
+            }
+            const unsigned pt = __popc(tb & z) & 1u;
+            const T cs = mats_s[op.mat];
+            if (x == 0) {
+                pauli_reg_diag(reg, cs.x, cs.y, zr, pt);
+            } else {
+                const int e = (__popc(x & z) + 3) & 3;  // -i * i^{#Y}
+                const float A = e == 0 ? 1.f : e == 2 ? -1.f : 0.f;
+                const float B = e == 1 ? -1.f : e == 3 ? 1.f : 0.f;
+                pauli_reg_dispatch(reg, xr, cs.x, cs.y * A, cs.y * B, -cs.y * B, cs.y * A, zr, pt);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kRegAmps; s++) tile[tb | roff[s]] = reg[s];
+        i += 1 + nseg;
+        __syncthreads();
+    }
+    if (vec) {
+        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
+            const unsigned l = p * 2;
+            *reinterpret_cast<uint4 *>(st + (hi_off[l >> L] | (l & Lmask))) =
+                *reinterpret_cast<const uint4 *>(tile + l);
+        }
+    } else {
+        for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_tile_pass_reg(TileArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_pass_body_reg(a, blockIdx.x, smem_raw);
+}
+
 // One pass of several independent states in one launch: descs[j] covers
 // blocks [cta_first_j, cta_first_{j+1}); each block finds its state's pass by
 // binary search and runs it on tile (blockIdx.x - cta_first_j).
@@ -757,6 +916,8 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 512, 2>));
     QSIM_ATTR((k_tile_pass<float, 256, 5>));
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
+    QSIM_ATTR(k_tile_pass_reg<256>);
+    QSIM_ATTR(k_tile_pass_reg<512>);
     QSIM_ATTR((k_tile_pass_multi<float, 256, 2>));
     QSIM_ATTR((k_tile_pass_multi<double, 256, 2>));
     QSIM_ATTR((k_tile_pass_multi<float, 512, 2>));
@@ -830,6 +991,18 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
         if (threads == 512) k_tile_pass<double, 512, 2><<<grid, 512, smem, s>>>(a);
         else k_tile_pass<double, 256, 2><<<grid, 256, smem, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_pass_reg(void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
+                                 uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
+                                 const MeasCtl *ctl, cudaStream_t s) {
+    if (m < 10 || m > 14) return cudaErrorInvalidValue;
+    TileArgs a;
+    if (!make_tile_args(0, state, n, m, tile_mask, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
+        return cudaErrorInvalidValue;
+    if (m <= 13) k_tile_pass_reg<256><<<1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s>>>(a);
+    else k_tile_pass_reg<512><<<1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s>>>(a);
     return cudaGetLastError();
 }
 

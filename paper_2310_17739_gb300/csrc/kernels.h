@@ -108,6 +108,14 @@ struct TileArgs {
 bool make_tile_args(int dtype, void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
                     uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
                     const MeasCtl *ctl, TileArgs *out);
+// A complex64 pass of rotations laid out in register segments (see
+// kSegMarker): 2^(m-5) threads, 32 amplitudes each; 10 <= m <= 14.
+cudaError_t launch_tile_pass_reg(void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
+                                 uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
+                                 const MeasCtl *ctl, cudaStream_t s);
+// Op-size marker of a register segment: lq[0..4] = the 5 tile positions held
+// in registers, flags = number of rotations that follow in the segment.
+constexpr uint8_t kSegMarker = 8;
 // Several states' passes in one launch: descs[0..n_desc) in device memory with
 // increasing cta_first; total_ctas blocks; max_m the largest tile among them.
 cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,

@@ -46,7 +46,9 @@ def parse():
                     help="gate count of the circuit (the named workload is 115,000,000)")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--k-max", type=int, default=2)
-    ap.add_argument("--fusion", type=int, default=1)
+    ap.add_argument("--fusion", type=int, default=-1,
+                    help="-1: autotune (paper fusion, k-qubit merge, Pauli-gadget rotations); "
+                         "0/1/2 force a fusion level")
     ap.add_argument("--profile-every", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -206,7 +208,14 @@ def run_ours(args):
     c = workload(args.gates)
     n = c.n
     zt = W.z_terms(n)
-    cfg = dict(fusion=args.fusion, k_max=args.k_max, tile_bits=args.tile_bits or 13)
+    sweep = None
+    if args.fusion < 0:
+        from paper_2310_17739_gb300 import autotune
+        cfg, entry = autotune.tune(n, c.gates, "c64", prefix=1_000_000, use_cache=False)
+        sweep = [dict(config=r["config"], gates_per_s=r["gates_per_s"], passes=r["passes"],
+                      fused_ops=r["fused_ops"]) for r in entry["report"]]
+    else:
+        cfg = dict(fusion=args.fusion, k_max=args.k_max, tile_bits=args.tile_bits or 13)
     stream = torch.cuda.current_stream()
     sim = qs.Sim(n, "c64", stream=stream, config=cfg, seed=1003)
     t0 = time.perf_counter()
@@ -312,8 +321,10 @@ def run_ours(args):
                                "exponentials per step, cycled) with 8 mid-circuit measurements",
                    "n_qubits": 21, "gates": c.G, "measurements": info["measurements"],
                    "fused_ops": info["fused_ops"], "passes": info["passes"],
-                   "fusion": "paper stages 1-4" if args.fusion == 1 else "none",
-                   "k_max": args.k_max, "tile_bits": cfg["tile_bits"],
+                   "fusion": {0: "none", 1: "paper stages 1-4",
+                              2: "paper stages 1-4 + Pauli-gadget rotations"}[cfg["fusion"]],
+                   "compile_config": cfg,
+                   "autotune_sweep_1M_gate_prefix": sweep,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed before the timed region; each step streams the ~%.1f GB program "
                          "(larger than L2); the 16 MiB state is L2-resident within a step by design"
@@ -347,7 +358,7 @@ def run_batched(args):
 
     cs, hams = W.config_batched()
     G = sum(c.G for c in cs)
-    fusion = 2 if args.fusion == 1 else args.fusion  # batched default: with gadget rotations
+    fusion = 2 if args.fusion < 0 else args.fusion  # default: with gadget rotations
     cfg = dict(fusion=fusion, k_max=args.k_max)
     stream = torch.cuda.current_stream()
     b = qs.Batch([c.n for c in cs], "c64", stream=stream, config=cfg, seeds=[0] * len(cs))
@@ -528,7 +539,7 @@ def run_serving(args):
     from paper_2310_17739_gb300 import qsim as qs
 
     pool = serving_pool(args.pool if hasattr(args, "pool") else 96)
-    fusion = 2 if args.fusion == 1 else args.fusion
+    fusion = 2 if args.fusion < 0 else args.fusion
     rng = np.random.default_rng(55)
     T = args.serve_seconds
     arrivals = []

@@ -376,20 +376,33 @@ QSIM_API qsim_status qsim_prob_noalloc(const void *d_state, int n_qubits, qsim_d
  * (then out_q[6i] = qubit, out_q[6i+1] = op code, out_q[6i+2] = flags);
  * out_q[6i .. 6i+k) = qubits, with bit j of the local matrix index = qubit
  * out_q[6i+j]; the 2^k x 2^k row-major complex matrix (interleaved doubles)
- * starts at out_mats[out_mat[i]].  Returns QSIM_E_INVAL when a capacity is too
+ * starts at out_mats[out_mat[i]].  out_k[i] = 7: a Pauli rotation
+ * i^g exp(-i theta P), P = i^{|x & z|} X^x Z^z, with x = out_q[6i] |
+ * out_q[6i+1] << 32, z = out_q[6i+2] | out_q[6i+3] << 32, g = out_q[6i+4] & 3,
+ * (cos theta, sin theta) at out_mats[out_mat[i]]; out_q[6i+4] bit 2 marks a
+ * Pauli-frame flush (theta = pi/2), which fusion level 2 emits before each
+ * measurement or reset and at the end of the stream.  Returns QSIM_E_INVAL when a capacity is too
  * small (*n_ops / *n_mat_doubles then give the sizes needed). */
 QSIM_API qsim_status qsim_fuse(int n_qubits, qsim_dtype dtype, const qsim_gate *gates, size_t n_gates,
                       const double *mats, size_t n_mats, const qsim_config *cfg,
                       uint8_t *out_k, uint32_t *out_q, uint64_t *out_mat, size_t cap_ops,
                       double *out_mats, size_t cap_mat_doubles,
                       size_t *n_ops, size_t *n_mat_doubles);
-/* qsim_schedule: the pass schedule of the same compile.  For pass i:
- * out_tile[i] = bit mask of the tile qubits (0 for a measurement pass),
- * out_first[i], out_count[i] = its range in the op order qsim_fuse returns. */
+/* qsim_schedule: the pass schedule of the same compile.  A pass's tile is a
+ * coset of an m-dimensional subspace V of the amplitude-index space GF(2)^n:
+ * tile element t is amplitude x0 ^ (XOR of basis[j] over the set bits j of
+ * t), the tile origin x0 ranging over the indices that are zero at every
+ * pivot of V.  A dense op needs the unit vector of each of its qubits in V; a
+ * Pauli rotation needs only its X mask in V.  With dense ops only, V is
+ * spanned by unit vectors and the tile is the classic set of m qubits.
+ * For pass i: out_tile[i] = the pivot positions of V (its qubits when V is
+ * spanned by unit vectors; 0 for a measurement pass); out_first[i],
+ * out_count[i] = its range in the op order qsim_fuse returns; if out_basis is
+ * not NULL, out_basis[16 i + j] = basis vector j (j < m; the rest 0). */
 QSIM_API qsim_status qsim_schedule(int n_qubits, qsim_dtype dtype, const qsim_gate *gates, size_t n_gates,
                           const double *mats, size_t n_mats, const qsim_config *cfg,
                           uint64_t *out_tile, uint64_t *out_first, uint32_t *out_count,
-                          size_t cap, size_t *n_passes);
+                          uint64_t *out_basis, size_t cap, size_t *n_passes);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,8 @@
 #include "compiler.h"
 #include "kernels.h"
 
+#include <cmath>
+
 static_assert(qsim::kTilePassOps == qsim::kPassOps && qsim::kTilePassMats == qsim::kPassMats,
               "the compiler's per-pass limits must match the tile kernel's shared-memory slices");
 
@@ -38,6 +40,7 @@ struct Packed {
     std::vector<DevOp> ops;
     std::vector<unsigned char> mats;
     std::vector<Pass> passes;
+    std::vector<uint64_t> bvec;  // tile bases (Pass::basis indexes it)
     int n = 0, m = 0;
     bool resident = false;
     uint64_t gates = 0, measurements = 0, fused = 0, dense_passes = 0;
@@ -51,13 +54,14 @@ struct DevChunk {
     void *d_mats = nullptr;
     size_t mats_bytes = 0;
     std::vector<Pass> passes;
+    std::vector<uint64_t> bvec;
     int m = 0;
     int kmax = 2;
     bool resident = false;
     uint64_t measurements = 0;
 };
 
-void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
+void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
     pk.n = hp.n;
     pk.m = hp.m;
     pk.resident = hp.resident;
@@ -75,14 +79,37 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
     } else if (!hp.pool.empty()) {
         std::memcpy(pk.mats.data(), hp.pool.data(), hp.pool.size() * 16);
     }
-    // Ops are re-emitted pass by pass; a complex64 pass made only of rotations
-    // whose X masks have <= 5 tile qubits is laid out in register segments
-    // (a kSegMarker op, then its rotations) for the register tile kernel.
+    // Ops are re-emitted pass by pass in tile coordinates (see Pass): a dense
+    // op's qubits become the tile bits of their unit vectors; a rotation
+    // exp(-i theta P), P = i^y X^xm Z^zm (y = #Y), becomes its X mask's
+    // coordinates xt, its Z mask's parities over the basis zt (bit j =
+    // parity(zm & basis_j)) and over the tile origin zc (zm gathered from the
+    // non-pivot positions, which the block index spreads x0 over), plus the
+    // factor -i i^y = i^e folded into its coefficient (cos theta, W):
+    //   a'_j = cos a_j + W (odd ? i : 1) (-1)^{parity(k & zm)} a_k,  k = j ^ xm,
+    // with W = +-sin theta and odd = e & 1 in lq[4] bit 0.
+    // A complex64 pass made only of rotations whose X coordinates have <= 5
+    // bits is laid out in register segments (a kSegMarker op, then its
+    // rotations, each with its X and Z coordinates over the segment's five
+    // register positions in lq[4] bits 1..5 and lq[5]) for the register
+    // tile kernel.
     pk.passes.clear();
     pk.ops.clear();
     pk.ops.reserve(hp.ops.size() + hp.passes.size() * 2);
+    pk.bvec = hp.bvec;
     uint64_t fused = 0, dp = 0;
     const bool reg_dtype = dt == QSIM_C64 && !hp.resident && hp.m >= 10 && hp.m <= 14;
+    auto set_coef = [&](uint64_t idx, double c, double w) {
+        if (dt == QSIM_C64) {
+            float *f = reinterpret_cast<float *>(pk.mats.data()) + 2 * idx;
+            f[0] = (float)c;
+            f[1] = (float)w;
+        } else {
+            double *f = reinterpret_cast<double *>(pk.mats.data()) + 2 * idx;
+            f[0] = c;
+            f[1] = w;
+        }
+    };
     for (const Pass &src : hp.passes) {
         Pass p = src;
         p.first = pk.ops.size();
@@ -99,71 +126,189 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
             continue;
         }
         dp++;
-        auto local = [&](uint64_t q) {
-            return (uint32_t)__builtin_popcountll(src.tile & ((1ull << q) - 1ull));
-        };
-        auto to_local = [&](uint64_t mask) {
-            uint32_t l = 0;
-            for (int q = 0; q < 64; q++)
-                if ((mask >> q) & 1) l |= 1u << local(q);
-            return l;
+        const int m = hp.resident ? hp.n : hp.m;
+        uint64_t *B = pk.bvec.data() + src.basis;
+        const uint64_t nonpiv = ~src.tile & (hp.n >= 64 ? ~0ull : ((1ull << hp.n) - 1));
+        auto gather = [&](uint64_t v) {  // v's bits at the non-pivot positions, packed
+            uint32_t r = 0;
+            int j = 0;
+            for (int b = 0; b < hp.n; b++)
+                if ((nonpiv >> b) & 1) r |= (uint32_t)((v >> b) & 1) << j++;
+            return r;
         };
         std::vector<DevOp> body;
-        body.reserve(src.count);
         bool all_rot = true;
-        for (uint64_t i = src.first; i < src.first + src.count; i++) {
-            const qsim::FOp &o = hp.ops[i];
-            DevOp d;
-            std::memset(&d, 0, sizeof(d));
-            d.k = o.k;
-            if (o.pauli()) {  // tile-local X and Z masks (<= 15 bits each) in lq[0..3]
-                const uint32_t lx = to_local(o.xm), lz = to_local(o.zm);
-                d.lq[0] = (uint8_t)(lx & 0xff);
-                d.lq[1] = (uint8_t)(lx >> 8);
-                d.lq[2] = (uint8_t)(lz & 0xff);
-                d.lq[3] = (uint8_t)(lz >> 8);
-                if (__builtin_popcount(lx) > 5) all_rot = false;
-            } else {
-                for (int j = 0; j < o.k; j++) d.lq[j] = (uint8_t)local(o.q[j]);
-                all_rot = false;
+        auto emit_body = [&]() {
+            qsim::Subspace S;
+            for (int j = 0; j < m; j++) S.add(B[j]);
+            body.clear();
+            all_rot = true;
+            for (uint64_t i = src.first; i < src.first + src.count; i++) {
+                const qsim::FOp &o = hp.ops[i];
+                DevOp d;
+                std::memset(&d, 0, sizeof(d));
+                d.k = o.k;
+                // the tile kernel indexes the pass's own coefficient slice; the
+                // resident kernel walks the whole pool
+                d.mat = (uint32_t)(hp.resident ? o.mat : o.mat - src.mat_first);
+                if (o.pauli()) {
+                    const uint32_t lx = S.coords(o.xm);
+                    uint32_t lz = 0;
+                    for (int j = 0; j < m; j++) lz |= (uint32_t)(__builtin_popcountll(o.zm & B[j]) & 1) << j;
+                    const uint32_t zc = gather(o.zm);
+                    d.lq[0] = (uint8_t)(lx & 0xff);
+                    d.lq[1] = (uint8_t)(lx >> 8);
+                    d.lq[2] = (uint8_t)(lz & 0xff);
+                    d.lq[3] = (uint8_t)(lz >> 8);
+                    // -i i^y, times i^g for a frame flush (whose cos is 0)
+                    const int e = (__builtin_popcountll(o.xm & o.zm) + 3 + (o.flags & qsim::kPhaseMask)) & 3;
+                    d.lq[4] = (uint8_t)(e & 1);
+                    d.flags = (uint16_t)(zc & 0xffff);
+                    d.pad = (uint16_t)(zc >> 16);
+                    const cd cs = hp.pool[o.mat];
+                    set_coef(o.mat, cs.real(), e >= 2 ? -cs.imag() : cs.imag());
+                    if (__builtin_popcount(lx) > 5) all_rot = false;
+                } else {
+                    for (int j = 0; j < o.k; j++) d.lq[j] = (uint8_t)__builtin_ctz(S.coords(1ull << o.q[j]));
+                    all_rot = false;
+                }
+                body.push_back(d);
             }
-            // the tile kernel indexes the pass's own coefficient slice; the
-            // resident kernel walks the whole pool
-            d.mat = (uint32_t)(hp.resident ? o.mat : o.mat - src.mat_first);
-            body.push_back(d);
-            fused++;
+        };
+        emit_body();
+        bool reg = allow_reg && reg_dtype && all_rot && src.gadget && hp.n <= 32;
+        if (reg) {
+            // scaled form: every cosine is >= 1/sqrt(2) after the Pauli frame
+            double scale = 1.0;
+            for (uint64_t i = src.first; i < src.first + src.count && reg; i++) {
+                const cd cs = hp.pool[hp.ops[i].mat];
+                if (std::fabs(cs.real()) < 0.5) reg = false;
+                scale *= cs.real();
+            }
+            if (reg) {
+                for (uint64_t i = src.first; i < src.first + src.count; i++) {
+                    const qsim::FOp &o = hp.ops[i];
+                    const cd cs = hp.pool[o.mat];
+                    const int e = (__builtin_popcountll(o.xm & o.zm) + 3 + (o.flags & qsim::kPhaseMask)) & 3;
+                    const double w = e >= 2 ? -cs.imag() : cs.imag();
+                    set_coef(o.mat, cs.real(), w / cs.real());
+                }
+                p.scale = (float)scale;
+            }
         }
-        if (reg_dtype && all_rot) {
+        if (!reg && src.gadget) {
+            // the generic tile kernel wants the basis vectors after the leading
+            // unit ones free of those low bits (whole 16-byte runs per row)
+            int l = 0;
+            while (l < m && B[l] == (1ull << l)) l++;
+            const uint64_t low = l >= 64 ? ~0ull : ((1ull << l) - 1);
+            for (int j = l; j < m; j++) B[j] &= ~low;
+            emit_body();
+        }
+        fused += body.size();
+        if (reg) {
             // greedy segments: grow the register set with each rotation's X
             // positions while it stays <= 5; fill it up with the highest free
             // positions (so that the lowest tile positions index threads)
             std::vector<std::pair<uint32_t, std::vector<DevOp>>> segs;
+            std::vector<float> tab;  // the pass's coefficient tables (floats)
+            const float *tvals_f = reinterpret_cast<const float *>(pk.mats.data());
+            std::vector<float> tvals(src.mat_count);  // t of each rotation, by relative coefficient index
+            for (uint32_t q = 0; q < src.mat_count; q++) tvals[q] = tvals_f[2 * (src.mat_first + q) + 1];
             uint32_t R = 0;
             std::vector<DevOp> cur;
             auto close = [&]() {
                 if (cur.empty()) return;
-                for (int b = src.tile ? __builtin_popcountll(src.tile) - 1 : 0; b >= 0 && __builtin_popcount(R) < 5; b--)
-                    R |= 1u << b;
+                for (int b = m - 1; b >= 0 && __builtin_popcount(R) < 5; b--) R |= 1u << b;
+                int pos[5];
+                for (int b = 0, j = 0; b < 32; b++)
+                    if ((R >> b) & 1) pos[j++] = b;
+                for (DevOp &d : cur) {
+                    const uint32_t x = d.lq[0] | ((uint32_t)d.lq[1] << 8);
+                    const uint32_t z = d.lq[2] | ((uint32_t)d.lq[3] << 8);
+                    uint32_t xr = 0, zr = 0;
+                    for (int j = 0; j < 5; j++) {
+                        xr |= ((x >> pos[j]) & 1u) << j;
+                        zr |= ((z >> pos[j]) & 1u) << j;
+                    }
+                    const float t = tvals[d.mat];
+                    qsim::RegRot r;
+                    std::memset(&r, 0, sizeof(r));
+                    r.k = qsim::kPauli;
+                    r.sel = (uint8_t)((d.lq[4] & 1) | (xr << 1));
+                    r.zt = (uint16_t)z;
+                    r.zc = d.flags | ((uint32_t)d.pad << 16);
+                    r.tab = (uint32_t)tab.size();
+                    // u over the pairs (slots for xr = 0), then negated
+                    const int H = xr ? 31 - __builtin_clz(xr) : -1;
+                    const int cnt = xr ? 16 : 32;
+                    float u[32];
+                    for (int q = 0; q < cnt; q++) {
+                        const uint32_t j = H < 0 ? (uint32_t)q : (((uint32_t)q >> H) << (H + 1)) | ((uint32_t)q & ((1u << H) - 1));
+                        u[q] = (__builtin_popcount(j & zr) & 1) ? -t : t;
+                    }
+                    for (int q = 0; q < cnt; q++) tab.push_back(u[q]);
+                    for (int q = 0; q < cnt; q++) tab.push_back(-u[q]);
+                    std::memcpy(&d, &r, sizeof(d));
+                }
                 segs.emplace_back(R, cur);
                 cur.clear();
                 R = 0;
             };
-            for (const DevOp &d : body) {
-                const uint32_t x = d.lq[0] | ((uint32_t)d.lq[1] << 8);
-                if ((x & ~R) && __builtin_popcount(R | x) > 5) close();
-                R |= x;
-                cur.push_back(d);
+            // List scheduling over the pass's rotations: an op is ready once
+            // every earlier op it does not commute with is placed; a segment
+            // takes ready ops whose X coordinates it already holds first, then
+            // the ready op that grows it least, and closes when none fits.
+            const size_t K = body.size();
+            std::vector<std::vector<uint32_t>> succ(K);  // later ops that must wait for this one
+            std::vector<uint32_t> waits(K, 0);
+            for (size_t a = 0; a < K; a++)
+                for (size_t b = a + 1; b < K; b++)
+                    if (!qsim::ops_commute(hp.ops[src.first + a], hp.ops[src.first + b])) {
+                        succ[a].push_back((uint32_t)b);
+                        waits[b]++;
+                    }
+            std::vector<char> placed(K, 0);
+            size_t left = K;
+            while (left) {
+                int best = -1, best_grow = 6;
+                for (size_t a = 0; a < K; a++) {
+                    if (placed[a] || waits[a]) continue;
+                    const uint32_t x = body[a].lq[0] | ((uint32_t)body[a].lq[1] << 8);
+                    const int grow = __builtin_popcount(x & ~R);
+                    if (__builtin_popcount(R | x) <= 5 && grow < best_grow) {
+                        best = (int)a;
+                        best_grow = grow;
+                        if (!grow) break;
+                    }
+                }
+                if (best < 0) {  // nothing ready fits: a new segment
+                    close();
+                    continue;
+                }
+                R |= body[best].lq[0] | ((uint32_t)body[best].lq[1] << 8);
+                cur.push_back(body[best]);
+                placed[best] = 1;
+                for (uint32_t b : succ[best]) waits[b]--;
+                left--;
             }
             close();
-            if (body.size() + segs.size() <= (size_t)qsim::kPassOps) {
+            if (body.size() + segs.size() <= (size_t)qsim::kPassOps && tab.size() <= 2 * (size_t)qsim::kPassMats) {
+                // the tables replace the pass's coefficient slice (appended)
+                while (pk.mats.size() % 16) pk.mats.push_back(0);
+                p.mat_first = pk.mats.size() / 8;
+                p.mat_count = (uint32_t)((tab.size() + 1) / 2);
+                const size_t off = pk.mats.size();
+                pk.mats.resize(off + (size_t)p.mat_count * 8, 0);
+                std::memcpy(pk.mats.data() + off, tab.data(), tab.size() * sizeof(float));
                 for (auto &sg : segs) {
-                    DevOp m;
-                    std::memset(&m, 0, sizeof(m));
-                    m.k = qsim::kSegMarker;
-                    m.flags = (uint16_t)sg.second.size();
+                    DevOp mk;
+                    std::memset(&mk, 0, sizeof(mk));
+                    mk.k = qsim::kSegMarker;
+                    mk.flags = (uint16_t)sg.second.size();
                     for (int b = 0, j = 0; b < 32; b++)
-                        if ((sg.first >> b) & 1) m.lq[j++] = (uint8_t)b;
-                    pk.ops.push_back(m);
+                        if ((sg.first >> b) & 1) mk.lq[j++] = (uint8_t)b;
+                    pk.ops.push_back(mk);
                     pk.ops.insert(pk.ops.end(), sg.second.begin(), sg.second.end());
                 }
                 p.reg = 1;
@@ -171,6 +316,10 @@ void pack(const HostProgram &hp, qsim_dtype dt, Packed &pk) {
                 pk.passes.push_back(p);
                 continue;
             }
+            // too many ops for one register-segment pass: the generic kernel
+            // runs it, with plain (cos, W) coefficients
+            emit_body();
+            p.scale = 1.0f;
         }
         pk.ops.insert(pk.ops.end(), body.begin(), body.end());
         p.count = (uint32_t)(pk.ops.size() - p.first);
@@ -210,6 +359,7 @@ struct qsim_ctx {
     uint64_t seed = 0;
     double thr = 0.0;
     Config cfg;
+    bool multi_state = false;  // a batch instance: its passes run in multi-state launches
     MeasCtl *h_ctl = nullptr;  // pinned readback of the control block
     std::vector<Staging> staging;
     std::string err;
@@ -358,6 +508,7 @@ qsim_status upload_chunk(qsim_ctx *c, const Packed &pk, DevChunk &dc) {
     dc.n_ops = pk.ops.size();
     dc.mats_bytes = pk.mats.size();
     dc.passes = pk.passes;
+    dc.bvec = pk.bvec;
     dc.m = pk.m;
     dc.kmax = 1;  // largest dense op (Pauli rotations, hist[7], run in every variant)
     for (int k = 5; k >= 1; k--)
@@ -448,12 +599,14 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
         const bool sample = c->prof_every > 0 && c->prof_launches % (uint64_t)c->prof_every == 0 &&
                             c->prof_used < c->prof_ev.size();
         if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
-        if (p.reg && c->cfg.threads == 0)
-            CK(qsim::launch_tile_pass_reg(c->state, c->n, dc.m, p.tile, dc.d_ops + p.first, p.count, dc.d_mats,
-                                          (uint32_t)p.mat_first, p.mat_count, c->ctl, c->stream),
-               "register tile pass launch");
+        const uint64_t *basis = dc.bvec.data() + p.basis;
+        if (p.reg)
+            CK(qsim::launch_rot_pass(c->state, c->n, dc.m, p.tile, basis, dc.d_ops + p.first, p.count,
+                                     dc.d_mats, (uint32_t)p.mat_first, p.mat_count, p.scale, c->ctl,
+                                     c->stream),
+               "rotation pass launch");
         else
-            CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile,
+            CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile, basis,
                                       dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
                                       p.mat_count, c->ctl, c->stream),
                "tile pass launch");
@@ -472,6 +625,10 @@ size_t chunk_size(const qsim_ctx *c) {
     return c->cfg.chunk_gates > 0 ? (size_t)c->cfg.chunk_gates : ((size_t)1 << 20);
 }
 
+// Register-segment layout for rotation passes: single-state launches with the
+// default thread count only (the multi-state kernel runs the generic pass).
+bool allow_reg(const qsim_ctx *c) { return c->cfg.threads == 0 && !c->multi_state; }
+
 int compile_threads(const qsim_ctx *c) {
     if (c->cfg.compile_threads > 0) return c->cfg.compile_threads;
     unsigned h = std::thread::hardware_concurrency();
@@ -489,7 +646,7 @@ qsim_status compile_chunks(qsim_ctx *c, const qsim_gate *g, size_t ng, const dou
         HostProgram hp;
         qsim::compile(c->n, c->dtype, c->cfg, g, ng, mats, nm, hp);
         Packed pk;
-        pack(hp, c->dtype, pk);
+        pack(hp, c->dtype, allow_reg(c), pk);
         return sink(pk);
     }
     const int T = std::min<int>(compile_threads(c), (int)nchunks);
@@ -513,7 +670,7 @@ qsim_status compile_chunks(qsim_ctx *c, const qsim_gate *g, size_t ng, const dou
             HostProgram hp;
             qsim::compile(c->n, c->dtype, c->cfg, g + b, e - b, mats, nm, hp);
             auto pk = std::make_unique<Packed>();
-            pack(hp, c->dtype, *pk);
+            pack(hp, c->dtype, allow_reg(c), *pk);
             {
                 std::lock_guard<std::mutex> lk(mu);
                 slots[i] = std::move(pk);
@@ -984,6 +1141,7 @@ qsim_status qsim_fuse(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, co
             out_q[6 * i + 1] = (uint32_t)(o.xm >> 32);
             out_q[6 * i + 2] = (uint32_t)o.zm;
             out_q[6 * i + 3] = (uint32_t)(o.zm >> 32);
+            out_q[6 * i + 4] = o.flags;
             out_mat[i] = o.mat * 2;
         } else if (o.k) {
             for (int j = 0; j < o.k; j++) out_q[6 * i + j] = o.q[j];
@@ -1003,7 +1161,7 @@ qsim_status qsim_fuse(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, co
 
 qsim_status qsim_schedule(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, const double *mats,
                           size_t nm, const qsim_config *cfg, uint64_t *out_tile, uint64_t *out_first,
-                          uint32_t *out_count, size_t cap, size_t *n_passes) {
+                          uint32_t *out_count, uint64_t *out_basis, size_t cap, size_t *n_passes) {
     if (n < 1 || n > 34 || (ng && !g)) return fail(nullptr, QSIM_E_INVAL, "bad arguments");
     std::string err;
     if (!qsim::validate(n, g, ng, mats, nm, err)) return fail(nullptr, QSIM_E_INVAL, err);
@@ -1015,6 +1173,12 @@ qsim_status qsim_schedule(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng
         out_tile[i] = hp.passes[i].ev ? 0 : hp.passes[i].tile;
         out_first[i] = hp.passes[i].first;
         out_count[i] = hp.passes[i].count;
+        if (out_basis) {
+            for (int j = 0; j < 16; j++) out_basis[16 * i + j] = 0;
+            if (!hp.passes[i].ev)
+                for (int j = 0; j < (hp.resident ? hp.n : hp.m); j++)
+                    out_basis[16 * i + j] = hp.bvec[hp.passes[i].basis + j];
+        }
     }
     return QSIM_OK;
 }
@@ -1145,6 +1309,7 @@ qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dty
     for (int i = 0; i < count; i++) {
         const int n = n_qubits[i];
         s = qsim_create(n, dtype, stream, alloc, free_fn, user, &b->inst[i]);
+        if (s == QSIM_OK) b->inst[i]->multi_state = true;
         if (s != QSIM_OK) {
             qsim_batch_destroy(b.release());
             return s;
@@ -1202,7 +1367,7 @@ qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *g, siz
         HostProgram hp;
         qsim::compile(c->n, c->dtype, c->cfg, g, ng, mats, nm, hp);
         Packed pk;
-        pack(hp, c->dtype, pk);
+        pack(hp, c->dtype, false, pk);
         s = sink(pk);
     } else {
         s = compile_chunks(c, g, ng, mats, nm, sink);
@@ -1237,9 +1402,9 @@ qsim_status build_tiled_plan(qsim_batch *b, bool may_upload) {
                     st.events.emplace_back(i, p);
                 } else {
                     qsim::TileArgs a;
-                    if (!qsim::make_tile_args(b->dtype, ic->state, ic->n, dc.m, p.tile, dc.d_ops + p.first,
-                                              p.count, dc.d_mats, (uint32_t)p.mat_first, p.mat_count,
-                                              ic->ctl, &a))
+                    if (!qsim::make_tile_args(b->dtype, ic->state, ic->n, dc.m, p.tile, dc.bvec.data() + p.basis,
+                                              dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
+                                              p.mat_count, ic->ctl, &a))
                         return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernel");
                     a.pad = (uint32_t)std::max(dc.kmax, 1);  // op size, read back below
                     b->tiled_descs.push_back(a);
@@ -1630,7 +1795,7 @@ void server_compile_loop(qsim_server *s) {
         HostProgram hp;
         qsim::compile(r->n, s->dtype, c, r->gates.data(), r->gates.size(), r->mats.data(), r->mats.size(), hp);
         Packed pk;
-        pack(hp, s->dtype, pk);
+        pack(hp, s->dtype, s->cfg.threads == 0, pk);
         r->n_meas = pk.measurements;
         r->device_bytes = ((size_t)(s->dtype == QSIM_C64 ? 8 : 16) << r->n) + pk.ops.size() * sizeof(DevOp) +
                           pk.mats.size() + (size_t)std::max<uint64_t>(r->n_meas, 1024) * sizeof(MeasRec) +

@@ -651,6 +651,32 @@ void merge_pass(std::vector<FOp> &ops, std::vector<cd> &pool, size_t first, size
 }  // namespace
 
 // ---------------------------------------------------------------- schedule --
+namespace {
+
+// Whether op o fits the tile subspace V within m dimensions (see Pass).
+bool fits(const Subspace &V, const FOp &o, int m) {
+    if (o.pauli()) return V.d < m || V.contains(o.xm);
+    uint64_t r[kMaxK];
+    int rank = 0;
+    for (int j = 0; j < o.k; j++) {
+        uint64_t v = V.reduce(1ull << o.q[j]);
+        for (int i = 0; i < rank; i++)
+            if ((v >> __builtin_ctzll(r[i])) & 1) v ^= r[i];
+        if (v) r[rank++] = v;
+    }
+    return V.d + rank <= m;
+}
+
+void take(Subspace &V, const FOp &o) {
+    if (o.pauli()) {
+        V.add(o.xm);
+    } else {
+        for (int j = 0; j < o.k; j++) V.add(1ull << o.q[j]);
+    }
+}
+
+}  // namespace
+
 void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, size_t n_gates,
              const double *mats, size_t n_mats, HostProgram &out) {
     out = HostProgram();
@@ -659,14 +685,13 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
     std::vector<FOp> ops;
     std::vector<cd> pool;
     const int m = tile_bits_for(cfg, n, dtype);
-    // a rotation must fit one tile together with nothing else
-    fuse(n, g, n_gates, mats, n_mats, cfg.fusion, ops, pool, &out.measurements, m);
+    // a rotation needs one tile dimension for its X mask, whatever its weight
+    fuse(n, g, n_gates, mats, n_mats, cfg.fusion, ops, pool, &out.measurements, 64);
 
     out.m = m;
     out.resident = (m == n);
     const int L = forced_low_bits(dtype, m);
     const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
-    const uint64_t forced = out.resident ? all : ((1ull << L) - 1);
     const size_t W = cfg.lookahead > 0 ? (size_t)cfg.lookahead : 64;
     const int k_max = std::max(2, std::min(cfg.k_max > 0 ? cfg.k_max : 2, std::min(5, m)));
 
@@ -692,11 +717,102 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
     std::vector<size_t> taken;
     std::vector<int64_t> skipped_pauli;
 
+    // Pauli frame.  The state on the device is F^dagger times the circuit's
+    // state, F = i^k X^x Z^z.  A rotation exp(-i theta P) reaches the device
+    // as exp(-i s theta P), s = -1 when P anticommutes with F; one with
+    // |cos theta| < |sin theta| is split as exp(-i (theta -+ pi/2) P) (-+ i P)
+    // and the Pauli factor joins the frame (F <- F (-+ i P)), so every
+    // rotation on the device has |cos| >= 1/sqrt(2).  A dense op U reaches it
+    // as F^dagger U F (F restricted to its qubits).  Before a measurement or
+    // reset, and at the end of the program, a flush op applies F to the state
+    // (F = i^{k - y + 1} exp(-i pi/2 P_F), P_F = i^y X^x Z^z, y = |x & z|).
+    struct Frame {
+        uint64_t x = 0, z = 0;
+        int k = 0;
+        bool trivial() const { return !x && !z && !(k & 3); }
+    } F;
+    auto frame_apply = [&](FOp &c) {
+        cd *M = &spool[c.mat];
+        if (c.pauli()) {
+            double cs = M[0].real(), sn = M[0].imag();
+            if ((popc(F.x & c.zm) + popc(F.z & c.xm)) & 1) sn = -sn;
+            if (std::fabs(cs) < std::fabs(sn)) {
+                const int y = popc(c.xm & c.zm);
+                int qk;
+                if (sn > 0) {  // theta' = theta - pi/2, factor -iP = i^{3+y} X Z
+                    const double t = cs;
+                    cs = sn;
+                    sn = -t;
+                    qk = 3 + y;
+                } else {       // theta' = theta + pi/2, factor iP = i^{1+y} X Z
+                    const double t = cs;
+                    cs = -sn;
+                    sn = t;
+                    qk = 1 + y;
+                }
+                F.k = (F.k + qk + 2 * popc(F.z & c.xm)) & 3;
+                F.x ^= c.xm;
+                F.z ^= c.zm;
+            }
+            M[0] = cd(cs, sn);
+            return;
+        }
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < c.k; j++) {
+            a |= (uint32_t)((F.x >> c.q[j]) & 1) << j;
+            b |= (uint32_t)((F.z >> c.q[j]) & 1) << j;
+        }
+        if (!a && !b) return;
+        const int D = 1 << c.k;
+        std::vector<cd> T(M, M + (size_t)D * D);
+        for (int r = 0; r < D; r++)
+            for (int q = 0; q < D; q++) {
+                const cd v = T[(size_t)(r ^ a) * D + (q ^ a)];
+                M[(size_t)r * D + q] = ((popc(b & r) + popc(b & q)) & 1) ? -v : v;
+            }
+    };
+    auto frame_flush = [&]() {
+        if (F.trivial()) return;
+        FOp o;
+        o.k = kPauli;
+        o.xm = F.x;
+        o.zm = F.z;
+        o.flags = (uint16_t)(((F.k - popc(F.x & F.z) + 1) & 3) | kFrameFlush);
+        Pass p;
+        p.first = sched.size();
+        p.count = 1;
+        p.mat_first = spool.size();
+        p.mat_count = 1;
+        p.fpa = 8;
+        p.basis = (uint32_t)out.bvec.size();
+        if (out.resident) {
+            p.tile = all;
+            for (int b = 0; b < n; b++) out.bvec.push_back(1ull << b);
+        } else {
+            Subspace V;
+            if (L < m)
+                for (int b = 0; b < L; b++) V.add(1ull << b);
+            if (F.x) V.add(F.x);
+            for (int b = 0; b < n && V.d < m; b++) V.add(1ull << b);
+            int idx[Subspace::kCap];
+            for (int j = 0; j < V.d; j++) idx[j] = j;
+            std::sort(idx, idx + V.d, [&](int u, int v) { return V.piv[u] < V.piv[v]; });
+            for (int j = 0; j < V.d; j++) out.bvec.push_back(V.vec[idx[j]]);
+            p.tile = V.pivots;
+        }
+        o.mat = spool.size();
+        spool.push_back(cd(0.0, 1.0));
+        sched.push_back(o);
+        out.passes.push_back(p);
+        F = Frame();
+    };
+
     while (nxt[HEAD] != HEAD) {
         const int64_t f = nxt[HEAD];
         if (ops[f].k == 0) {  // event: its own pass, never reordered
             unlink(f);
             if (ops[f].ev != EV_BARRIER) {
+                frame_flush();
                 Pass p;
                 p.first = sched.size();
                 p.count = 1;
@@ -708,12 +824,18 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             }
             continue;
         }
-        // An op may join the pass if its qubits fit the tile and it commutes
-        // with every op skipped so far (disjoint qubits, or two commuting
-        // Pauli rotations), so pulling it ahead of them changes nothing.
-        // The forced low qubits (coalesced tile rows) are dropped for a pass
-        // whose first op would not fit beside them.
-        uint64_t T = popc(forced | ops[f].mask()) <= m ? forced : 0;
+        // An op may join the pass if the tile's subspace V can take it (see
+        // Pass) within m dimensions and it commutes with every op skipped so
+        // far (disjoint qubits, or two commuting Pauli rotations), so pulling
+        // it ahead of them changes nothing.  V starts with the forced low
+        // qubits (coalesced tile rows) unless the pass's first op would not
+        // fit beside them.  A resident program's tile is the whole state.
+        Subspace V;
+        if (!out.resident) {
+            for (int b = 0; b < L; b++) V.add(1ull << b);
+            if (!fits(V, ops[f], m)) V = Subspace();
+        }
+        bool only_rot = true;
         uint64_t blocked_np = 0, blocked_p = 0;
         size_t skipped = 0, n_mats = 0;
         taken.clear();
@@ -727,7 +849,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
                 n_mats + mat_entries(o) > (size_t)kTilePassMats)
                 break;
             const uint64_t Q = o.mask();
-            bool ok = popc(T | Q) <= m && !(Q & blocked_np);
+            bool ok = (out.resident || fits(V, o, m)) && !(Q & blocked_np);
             if (ok && (Q & blocked_p)) {
                 if (!o.pauli()) ok = false;
                 else
@@ -738,7 +860,8 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
                         }
             }
             if (ok) {
-                T |= Q;
+                if (!out.resident) take(V, o);
+                only_rot = only_rot && o.pauli();
                 taken.push_back((size_t)i);
                 n_mats += mat_entries(o);
                 unlink(i);
@@ -754,8 +877,28 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             }
             i = ni;
         }
-        // Pad the tile to exactly m qubits (lowest unused first).
-        for (int b = 0; b < n && popc(T) < m; b++) T |= 1ull << b;
+        // Pad V to exactly m dimensions with the lowest free unit vectors, and
+        // record the basis: a rotation-only pass keeps the vectors in the
+        // order they were added (each new rotation's X mask is one tile bit),
+        // any other pass the row-echelon basis by ascending pivot (then a
+        // qubit in V is the tile bit of its rank among the pivots).
+        uint64_t T;
+        const uint32_t bfirst = (uint32_t)out.bvec.size();
+        if (out.resident) {
+            T = all;
+            for (int b = 0; b < n; b++) out.bvec.push_back(1ull << b);
+        } else {
+            for (int b = 0; b < n && V.d < m; b++) V.add(1ull << b);
+            T = V.pivots;
+            if (only_rot) {
+                for (int j = 0; j < V.d; j++) out.bvec.push_back(V.added[j]);
+            } else {
+                int idx[Subspace::kCap];
+                for (int j = 0; j < V.d; j++) idx[j] = j;
+                std::sort(idx, idx + V.d, [&](int a, int b) { return V.piv[a] < V.piv[b]; });
+                for (int j = 0; j < V.d; j++) out.bvec.push_back(V.vec[idx[j]]);
+            }
+        }
         std::vector<FOp> body;
         body.reserve(taken.size());
         if (cfg.k_max > 2) {
@@ -773,6 +916,8 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
         auto open_pass = [&]() {
             p = Pass();
             p.tile = T;
+            p.basis = bfirst;
+            p.gadget = (uint8_t)(!out.resident && only_rot);
             p.first = sched.size();
             p.mat_first = spool.size();
         };
@@ -794,10 +939,12 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             FOp c = o;
             c.mat = spool.size();
             spool.insert(spool.end(), pool.begin() + o.mat, pool.begin() + o.mat + e);
+            frame_apply(c);
             sched.push_back(c);
         }
         close_pass();
     }
+    frame_flush();
     for (const FOp &o : sched)
         if (o.k) out.hist[o.k]++;
     out.ops.swap(sched);

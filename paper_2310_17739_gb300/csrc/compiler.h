@@ -27,6 +27,10 @@ enum : uint8_t { EV_NONE = 0, EV_MEASURE = 1, EV_RESET = 2, EV_BARRIER = 3 };
 // k == kPauli: a Pauli rotation exp(-i theta P) with P = i^{#Y} X^xm Z^zm on the
 // qubits of xm | zm (Y = bit in both); pool[mat] = (cos theta, sin theta).
 constexpr uint8_t kPauli = 7;
+// FOp::flags of a Pauli op: bits 0-1 = g, the op is i^g exp(-i theta P) (g != 0
+// only for a frame flush, whose cos theta is 0); bit 2 = frame flush.
+constexpr uint16_t kPhaseMask = 3;
+constexpr uint16_t kFrameFlush = 4;
 
 struct FOp {
     uint8_t k = 0;
@@ -53,10 +57,71 @@ inline bool ops_commute(const FOp &a, const FOp &b) {
     return false;
 }
 
-// A pass: full-state sweep over tiles of the qubits in `tile` applying ops
-// [first, first+count) in order; or an event pass (tile == 0, count == 1).
+// A linear subspace of GF(2)^n (bit q <-> qubit q) in reduced row-echelon
+// form: vec[i] has its lowest set bit at piv[i] and a zero at every other
+// pivot, so v is in the subspace iff reduce(v) == 0, and the coordinates of a
+// member are read off its pivot bits.  combo[i] is vec[i] written in the basis
+// of the vectors that add() accepted, in their order (bit j = the j-th).
+struct Subspace {
+    static constexpr int kCap = 16;
+    int d = 0;
+    uint64_t pivots = 0;
+    uint64_t vec[kCap];
+    uint32_t combo[kCap];
+    uint8_t piv[kCap];
+    uint64_t added[kCap];  // the accepted vectors, in order
+
+    uint64_t reduce(uint64_t v) const {
+        for (int i = 0; i < d; i++)
+            if ((v >> piv[i]) & 1) v ^= vec[i];
+        return v;
+    }
+    bool contains(uint64_t v) const { return reduce(v) == 0; }
+    // Adds v; returns false (and changes nothing) if v is already a member or
+    // the capacity is reached.
+    bool add(uint64_t v) {
+        if (d >= kCap) return false;
+        uint64_t r = v;
+        uint32_t c = 1u << d;
+        for (int i = 0; i < d; i++)
+            if ((r >> piv[i]) & 1) {
+                r ^= vec[i];
+                c ^= combo[i];
+            }
+        if (!r) return false;
+        const int p = __builtin_ctzll(r);
+        for (int i = 0; i < d; i++)
+            if ((vec[i] >> p) & 1) {
+                vec[i] ^= r;
+                combo[i] ^= c;
+            }
+        vec[d] = r;
+        combo[d] = c;
+        piv[d] = (uint8_t)p;
+        added[d] = v;
+        pivots |= 1ull << p;
+        d++;
+        return true;
+    }
+    // Coordinates of a member v in the basis added[0..d): bit j <-> added[j].
+    uint32_t coords(uint64_t v) const {
+        uint32_t c = 0;
+        for (int i = 0; i < d; i++)
+            if ((v >> piv[i]) & 1) c ^= combo[i];
+        return c;
+    }
+};
+
+// A pass: full-state sweep over tiles applying ops [first, first+count) in
+// order; or an event pass (tile == 0, count == 1).  A tile is a coset
+// x0 + V of an m-dimensional subspace V: tile element t (m bits) is amplitude
+// x0 ^ (XOR of basis[j] over the set bits j of t), with the tile's own x0
+// spread over the positions that are not pivots of V.  A dense op needs the
+// unit vector of each of its qubits in V (then that vector is a basis vector
+// and the qubit is one tile bit); a Pauli rotation needs only its X mask in V
+// (its Z part becomes a parity of the tile index and of x0).
 struct Pass {
-    uint64_t tile = 0;
+    uint64_t tile = 0;    // pivot positions of V (for unit-vector bases: the tile qubits)
     uint64_t first = 0;
     uint32_t count = 0;
     uint8_t ev = EV_NONE;
@@ -66,6 +131,10 @@ struct Pass {
     uint32_t fpa = 0;     // algorithmic real flops per amplitude of the pass (8 * 2^k per op)
     uint64_t mat_first = 0;  // the pass's coefficients: pool[mat_first, mat_first + mat_count)
     uint32_t mat_count = 0;
+    uint32_t basis = 0;   // the pass's m basis vectors: bvec[basis, basis + m) of its program
+    uint8_t gadget = 0;   // basis = X masks of its rotations in order (rotation-only pass);
+                          // otherwise the reduced row-echelon basis, ascending pivots
+    float scale = 1.0f;   // register-segment passes: product of the rotations' cosines
 };
 
 // Per-pass limits of the tile kernel (its ops and coefficients are copied
@@ -100,6 +169,7 @@ struct HostProgram {
     std::vector<FOp> ops;
     std::vector<cd> pool;
     std::vector<Pass> passes;
+    std::vector<uint64_t> bvec;  // tile bases of the passes (m per non-event pass)
     uint64_t gates = 0;
     uint64_t measurements = 0;
     uint64_t hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};

@@ -263,40 +263,41 @@ __device__ __forceinline__ void apply_dense_smem(T *tile, int m, const DevOp &op
     }
 }
 
-// Pauli rotation exp(-i theta P), P = i^{ny} X^x Z^z on tile-local masks:
-//   P|j> = ph(j)|j^x>,  ph(j) = i^{ny} (-1)^{popcount(j & z)},
-//   a'_j = cos(theta) a_j - i sin(theta) ph(j^x) a_{j^x}.
-// With x = 0 it is diagonal: a'_j = (cos - i sin (-1)^{popcount(j&z)}) a_j.
+// Pauli rotation in tile coordinates (encoding in kernels.h): with x, z the
+// tile-local X and Z masks, b = parity(zc & tile index), u = +-W,
+//   a'_j = cos a_j + W (odd ? i : 1) (-1)^{parity(k & z) ^ b} a_k,   k = j ^ x.
+// With x = 0 it is diagonal: a'_j = (cos + W (odd ? i : 1) (-1)^{parity(j & z) ^ b}) a_j.
 template <typename T, int NT>
-__device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, const T *mats) {
+__device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, const T *mats, uint32_t bid) {
     const unsigned x = op.lq[0] | ((unsigned)op.lq[1] << 8);
     const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
+    const bool odd = op.lq[4] & 1;
+    const uint32_t zc = op.flags | ((uint32_t)op.pad << 16);
     const T cs = mats[op.mat];
-    const auto c = cs.x, s = cs.y;
+    const auto c = cs.x;
+    const auto w = (__popc(zc & bid) & 1) ? -cs.y : cs.y;
     const unsigned Nt = 1u << m;
+    // (c, w) pair update: r = c a + u (odd ? i : 1) b
+    auto upd = [odd, c](T a, T b, decltype(c) u) {
+        T r;
+        if (odd) {
+            r.x = c * a.x - u * b.y;
+            r.y = c * a.y + u * b.x;
+        } else {
+            r.x = c * a.x + u * b.x;
+            r.y = c * a.y + u * b.y;
+        }
+        return r;
+    };
     if (x == 0) {
         for (unsigned j = threadIdx.x; j < Nt; j += NT) {
-            const auto sg = (__popc(j & z) & 1) ? -s : s;
+            const auto u = (__popc(j & z) & 1) ? -w : w;
             const T a = tile[j];
-            T r;
-            r.x = c * a.x + sg * a.y;  // (c - i sg)(ax + i ay)
-            r.y = c * a.y - sg * a.x;
-            tile[j] = r;
+            tile[j] = upd(a, a, u);
         }
         return;
     }
-    // -i * i^{ny} = i^{(ny + 3) mod 4}: multiply by one of 1, i, -1, -i
-    const int e = (__popc(x & z) + 3) & 3;
     const int low = __ffs(x) - 1;
-    // rotation of a complex number by i^e
-    auto rot = [e](T v) {
-        T r;
-        if (e == 0) { r.x = v.x; r.y = v.y; }
-        else if (e == 1) { r.x = -v.y; r.y = v.x; }
-        else if (e == 2) { r.x = -v.x; r.y = -v.y; }
-        else { r.x = v.y; r.y = -v.x; }
-        return r;
-    };
     // U pairs per thread per iteration, all loaded before any is stored (the
     // pairs are disjoint), so shared-memory latency overlaps across them
     constexpr int U = 4;
@@ -315,16 +316,10 @@ __device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, con
         for (int u = 0; u < U; u++) {
             if (g0 + u * NT >= P) break;
             const unsigned j = jj[u], k = j ^ x;
-            const auto sj = (__popc(j & z) & 1) ? -s : s;  // sin * (-1)^{popcount(j&z)}
-            const auto sk = (__popc(k & z) & 1) ? -s : s;
-            const T rk = rot(ak[u]), rj = rot(aj[u]);
-            T nj, nk;
-            nj.x = c * aj[u].x + sk * rk.x;
-            nj.y = c * aj[u].y + sk * rk.y;
-            nk.x = c * ak[u].x + sj * rj.x;
-            nk.y = c * ak[u].y + sj * rj.y;
-            tile[j] = nj;
-            tile[k] = nk;
+            const auto wk = (__popc(k & z) & 1) ? -w : w;  // W (-1)^{parity(k & z) ^ b}
+            const auto wj = (__popc(j & z) & 1) ? -w : w;
+            tile[j] = upd(aj[u], ak[u], wk);
+            tile[k] = upd(ak[u], aj[u], wj);
         }
     }
 }
@@ -332,9 +327,10 @@ __device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, con
 // STAGE: matrices come from global memory (k >= 3 ones are staged in mbuf);
 // otherwise `mats` is the pass's coefficient slice already in shared memory.
 template <typename T, int NT, int KMAX, bool STAGE = true>
-__device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const T *mats, T *mbuf) {
+__device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const T *mats, T *mbuf,
+                                         uint32_t bid) {
     switch (op.k) {
-        case 7: apply_pauli<T, NT>(tile, m, op, mats); break;
+        case 7: apply_pauli<T, NT>(tile, m, op, mats, bid); break;
         case 1: apply_dense_reg<1, T, NT>(tile, m, op, mats); break;
         case 2: apply_dense_reg<2, T, NT>(tile, m, op, mats); break;
         case 3: if constexpr (KMAX >= 3) apply_dense_smem<3, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
@@ -343,6 +339,14 @@ __device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const 
         default: break;
     }
 }
+
+// Programmatic dependent launch: a tile pass is launched while the previous
+// kernel on the stream is still running; it stages its program slice first
+// and waits for the previous grid (its completion and memory) before it
+// touches the state or the control block.  In a kernel launched without the
+// attribute the wait returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Asynchronous global -> shared copies (cp.async): issued without waiting,
 // completed by cp_async_wait_all (commit + wait for all of this thread's groups).
@@ -380,7 +384,7 @@ __device__ __forceinline__ void tile_pass_body(const TileArgs &a, const uint64_t
     T *mats_s = tile + (1u << a.m);                                   // kPassMats values
     DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);     // kPassOps ops
     __shared__ uint64_t hi_off[kMaxHi];
-    const int status = a.ctl->status;  // checked once everything is in flight
+    grid_dep_launch_next();
     // 1. the pass's ops and coefficients: asynchronous copies
     for (unsigned i = threadIdx.x; i < a.n_ops; i += NT) cp_async16(ops_s + i, a.ops + i);
     {
@@ -390,16 +394,20 @@ __device__ __forceinline__ void tile_pass_body(const TileArgs &a, const uint64_t
             else cp_async8(mats_s + i, gm + i);
         }
     }
-    // 2. global offsets of the tile rows: non-tile bits from blockIdx, tile bits
-    //    above the L contiguous low ones from the row index
+    // 2. global offsets of the tile rows: the tile origin spreads blockIdx over
+    //    the non-pivot positions; tile bits above the L contiguous low ones
+    //    (unit basis vectors) add their basis vectors
     uint64_t base = 0;
     for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << a.ntq[j];
     const int L = a.L, hib = a.m - L;
     for (int r = threadIdx.x; r < (1 << hib); r += NT) {
         uint64_t o = base;
-        for (int j = 0; j < hib; j++) o |= ((uint64_t)((r >> j) & 1)) << a.tq[L + j];
+        for (int j = 0; j < hib; j++)
+            if ((r >> j) & 1) o ^= a.bv[L + j];
         hi_off[r] = o;
     }
+    grid_dep_wait();
+    const int status = a.ctl->status;  // checked once everything is in flight
     __syncthreads();
     T *st = reinterpret_cast<T *>(a.state);
     const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
@@ -421,7 +429,7 @@ __device__ __forceinline__ void tile_pass_body(const TileArgs &a, const uint64_t
     if (status) return;  // a failed assertion earlier on this stream: leave the state
     for (uint32_t i = 0; i < a.n_ops; i++) {
         const DevOp op = ops_s[i];
-        apply_op<T, NT, KMAX, false>(tile, a.m, op, mats_s, nullptr);
+        apply_op<T, NT, KMAX, false>(tile, a.m, op, mats_s, nullptr, (uint32_t)bid);
         __syncthreads();
     }
     if (vec) {
@@ -442,162 +450,203 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a)
 }
 
 // ------------------------------------------------------ register segments --
-// complex64 rotation passes: each thread holds 32 amplitudes of the tile in
-// registers.  The pass is a list of segments (a kSegMarker op naming 5 tile
-// positions -- the "register qubits" -- followed by rotations whose X mask
-// lies within them); a rotation is then a butterfly between register slots s
-// and s ^ xr of one thread, with no shared-memory traffic and no barrier.
-// Shared memory is touched only to lay the tile out again between segments.
+// complex64 rotation passes over a tile of 2^m amplitudes (10 <= m <= 14):
+// 2^(m-5) threads of 32 amplitudes each.  The pass is a list of segments: a
+// kSegMarker op naming 5 tile positions R (the register positions), then
+// rotations whose X coordinates lie within R.  In a segment the thread's bits
+// run over the other m - 5 tile positions in ascending order (its lanes over
+// the lowest of them) and its 32 register slots over R, so a rotation is a
+// butterfly between slots s and s ^ xr of one thread: no shared memory and no
+// barrier.  The first segment gathers its amplitudes straight from global
+// memory and the last scatters them back; shared memory holds the tile only
+// to lay it out again between segments.
 constexpr int kRegAmps = 32;
 
-// a'_s = c a_s + (-1)^{par(s^xr)} sin * i^e a_{s^xr}, for both slots of each pair.
-// (sA, sB, sC, sD) = sin * (the 2x2 real form of multiplication by i^e).
-template <int XR>
-__device__ __forceinline__ void pauli_reg_pairs(float2 *a, float c, float sA, float sB, float sC,
-                                                float sD, unsigned zr, unsigned pt) {
+__host__ __device__ constexpr int top_bit(int v) { return v >= 16 ? 4 : v >= 8 ? 3 : v >= 4 ? 2 : v >= 2 ? 1 : 0; }
+
+__host__ __device__ constexpr int pair_lo(int p, int H) {  // p with a zero inserted at bit H
+    return ((p >> H) << (H + 1)) | (p & ((1 << H) - 1));
+}
+
+// Pairs (j, k = j ^ XR), j with XR's top bit clear, coefficient u[p] from the
+// rotation's table (see RegRot); in the scaled form (the cosine is applied
+// once per pass):
+//   ODD:  a'_j = a_j + i u a_k,   a'_k = a_k + i u a_j
+//   EVEN: a'_j = a_j - u a_k,     a'_k = a_k + u a_j
+template <int XR, bool ODD>
+__device__ __forceinline__ void rot_reg(float2 *a, const float4 *U) {
+    constexpr int H = top_bit(XR);
 #pragma unroll
-    for (int s = 0; s < kRegAmps; s++) {
-        const int q = s ^ XR;
-        if (s < q) {
-            const float fs = ((__popc((unsigned)s & zr) ^ pt) & 1u) ? -1.f : 1.f;
-            const float fq = ((__popc((unsigned)q & zr) ^ pt) & 1u) ? -1.f : 1.f;
-            const float2 as = a[s], aq = a[q];
-            float2 ns, nq;
-            ns.x = c * as.x + fq * (sA * aq.x + sB * aq.y);
-            ns.y = c * as.y + fq * (sC * aq.x + sD * aq.y);
-            nq.x = c * aq.x + fs * (sA * as.x + sB * as.y);
-            nq.y = c * aq.y + fs * (sC * as.x + sD * as.y);
-            a[s] = ns;
-            a[q] = nq;
+    for (int p = 0; p < 16; p++) {
+        const int j = pair_lo(p, H);
+        const int k = j ^ XR;
+        const float2 aj = a[j], ak = a[k];
+        const float4 v = U[p >> 2];
+        const float uj = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+        if (ODD) {
+            a[j] = make_float2(fmaf(-uj, ak.y, aj.x), fmaf(uj, ak.x, aj.y));
+            a[k] = make_float2(fmaf(-uj, aj.y, ak.x), fmaf(uj, aj.x, ak.y));
+        } else {
+            a[j] = make_float2(fmaf(-uj, ak.x, aj.x), fmaf(-uj, ak.y, aj.y));
+            a[k] = make_float2(fmaf(uj, aj.x, ak.x), fmaf(uj, aj.y, ak.y));
         }
     }
 }
 
-__device__ __forceinline__ void pauli_reg_diag(float2 *a, float c, float sn, unsigned zr, unsigned pt) {
+// No X part: a'_j = (1 + u_j (odd ? i : 1)) a_j, u_j from the 32-entry table.
+__device__ __forceinline__ void rot_reg_diag(float2 *a, const float4 *U, bool odd) {
 #pragma unroll
-    for (int s = 0; s < kRegAmps; s++) {
-        const float sg = ((__popc((unsigned)s & zr) ^ pt) & 1u) ? -sn : sn;
-        const float2 v = a[s];
-        a[s].x = c * v.x + sg * v.y;  // (c - i sg)(x + i y)
-        a[s].y = c * v.y - sg * v.x;
+    for (int q = 0; q < 8; q++) {
+        const float4 v = U[q];
+        const float u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int j = 4 * q + e;
+            const float2 w = a[j];
+            if (odd) a[j] = make_float2(fmaf(-u[e], w.y, w.x), fmaf(u[e], w.x, w.y));
+            else a[j] = make_float2(fmaf(u[e], w.x, w.x), fmaf(u[e], w.y, w.y));
+        }
     }
 }
 
-__device__ __forceinline__ void pauli_reg_dispatch(float2 *a, unsigned xr, float c, float sA, float sB,
-                                                float sC, float sD, unsigned zr, unsigned pt) {
-    switch (xr) {
-#define QSIM_XR(v) case v: pauli_reg_pairs<v>(a, c, sA, sB, sC, sD, zr, pt); break;
-        QSIM_XR(1) QSIM_XR(2) QSIM_XR(3) QSIM_XR(4) QSIM_XR(5) QSIM_XR(6) QSIM_XR(7) QSIM_XR(8)
-        QSIM_XR(9) QSIM_XR(10) QSIM_XR(11) QSIM_XR(12) QSIM_XR(13) QSIM_XR(14) QSIM_XR(15)
-        QSIM_XR(16) QSIM_XR(17) QSIM_XR(18) QSIM_XR(19) QSIM_XR(20) QSIM_XR(21) QSIM_XR(22)
-        QSIM_XR(23) QSIM_XR(24) QSIM_XR(25) QSIM_XR(26) QSIM_XR(27) QSIM_XR(28) QSIM_XR(29)
-        QSIM_XR(30) QSIM_XR(31)
-#undef QSIM_XR
+// sel = xr << 1 | odd (of a RegRot), xr != 0.
+__device__ __forceinline__ void rot_reg_dispatch(float2 *a, unsigned sel, const float4 *U) {
+    switch (sel) {
+#define QSIM_R(v)                                    \
+    case 2 * v: rot_reg<v, false>(a, U); break;      \
+    case 2 * v + 1: rot_reg<v, true>(a, U); break;
+        QSIM_R(1) QSIM_R(2) QSIM_R(3) QSIM_R(4) QSIM_R(5) QSIM_R(6) QSIM_R(7) QSIM_R(8)
+        QSIM_R(9) QSIM_R(10) QSIM_R(11) QSIM_R(12) QSIM_R(13) QSIM_R(14) QSIM_R(15)
+        QSIM_R(16) QSIM_R(17) QSIM_R(18) QSIM_R(19) QSIM_R(20) QSIM_R(21) QSIM_R(22)
+        QSIM_R(23) QSIM_R(24) QSIM_R(25) QSIM_R(26) QSIM_R(27) QSIM_R(28) QSIM_R(29)
+        QSIM_R(30) QSIM_R(31)
+#undef QSIM_R
         default: break;
     }
 }
 
-// Register-segment pass body (complex64, blockDim = 2^(m-5) threads).
-__device__ __forceinline__ void tile_pass_body_reg(const TileArgs &a, const uint64_t bid,
-                                                   unsigned char *smem_raw) {
-    using T = float2;
-    const unsigned NT = blockDim.x;
-    T *tile = reinterpret_cast<T *>(smem_raw);
-    T *mats_s = tile + (1u << a.m);
-    DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);
-    __shared__ uint64_t hi_off[kMaxHi];
-    __shared__ unsigned roff[kRegAmps];
-    const int status = a.ctl->status;
-    for (unsigned i = threadIdx.x; i < a.n_ops; i += NT) cp_async16(ops_s + i, a.ops + i);
-    {
-        const T *gm = reinterpret_cast<const T *>(a.mats) + a.mat_first;
-        for (unsigned i = threadIdx.x; i < a.mat_count; i += NT) cp_async8(mats_s + i, gm + i);
-    }
-    uint64_t base = 0;
-    for (int j = 0; j < a.n - a.m; j++) base |= ((bid >> j) & 1ull) << a.ntq[j];
-    const int L = a.L, hib = a.m - L;
-    for (int r = threadIdx.x; r < (1 << hib); r += NT) {
-        uint64_t o = base;
-        for (int j = 0; j < hib; j++) o |= ((uint64_t)((r >> j) & 1)) << a.tq[L + j];
-        hi_off[r] = o;
-    }
-    __syncthreads();
-    T *st = reinterpret_cast<T *>(a.state);
-    const unsigned Nt = 1u << a.m, Lmask = (1u << L) - 1u;
-    const bool vec = L >= 1;
-    if (vec) {
-        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
-            const unsigned l = p * 2;
-            cp_async16(tile + l, st + (hi_off[l >> L] | (l & Lmask)));
+// The rotations of one segment, on this thread's registers: each takes the
+// half of its coefficient table that matches the thread's Z parity (RegRot).
+__device__ __forceinline__ void seg_rotations(float2 *reg, const RegRot *ops, uint32_t count, uint32_t tb,
+                                              uint32_t bid, const float *coef) {
+    for (uint32_t k = 0; k < count; k++) {
+        const RegRot op = ops[k];
+        const uint32_t pt = (__popc(tb & op.zt) ^ __popc(op.zc & bid)) & 1u;
+        if (op.sel >> 1) {
+            rot_reg_dispatch(reg, op.sel, reinterpret_cast<const float4 *>(coef + op.tab + 16 * pt));
+        } else {
+            rot_reg_diag(reg, reinterpret_cast<const float4 *>(coef + op.tab + 32 * pt), op.sel & 1u);
         }
-    } else {
-        for (unsigned l = threadIdx.x; l < Nt; l += NT) cp_async8(tile + l, st + (hi_off[l >> L] | (l & Lmask)));
     }
-    cp_async_wait_all();
-    __syncthreads();
-    if (status) return;
-    T reg[kRegAmps];
-    uint32_t i = 0;
-    while (i < a.n_ops) {
-        const DevOp seg = ops_s[i];  // kSegMarker: lq[0..4] register positions, flags = #ops
-        const unsigned nseg = seg.flags;
-        unsigned rmask = 0;
+}
+
+// Slot s of a segment sits at tile index tb | sum of 2^pos[j] over the set
+// bits j of s.  The 32 slots are visited in Gray-code order, so each address
+// (shared-memory byte offset, or amplitude index by XOR of basis vectors)
+// follows from the previous one with one add or XOR.
+__host__ __device__ constexpr int gray(int i) { return i ^ (i >> 1); }
+__host__ __device__ constexpr int gray_flip(int i) {  // bit that changes from gray(i-1) to gray(i)
+    return (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4;
+}
+
+__device__ __forceinline__ void seg_store_smem(const float2 *reg, uint32_t addr, const uint32_t *d) {
 #pragma unroll
-        for (int j = 0; j < 5; j++) rmask |= 1u << seg.lq[j];
-        // this thread's tile index on the non-register positions
-        unsigned tb = 0;
-        for (int b = 0, j = 0; b < a.m; b++)
-            if (!((rmask >> b) & 1u)) tb |= ((threadIdx.x >> j++) & 1u) << b;
-        if (threadIdx.x < kRegAmps) {
-            unsigned o = 0;
-#pragma unroll
-            for (int j = 0; j < 5; j++) o |= ((threadIdx.x >> j) & 1u) << seg.lq[j];
-            roff[threadIdx.x] = o;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < kRegAmps; s++) reg[s] = tile[tb | roff[s]];
-        for (uint32_t k = 1; k <= nseg; k++) {
-            const DevOp op = ops_s[i + k];
-            const unsigned x = op.lq[0] | ((unsigned)op.lq[1] << 8);
-            const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
-            unsigned xr = 0, zr = 0;
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                xr |= ((x >> seg.lq[j]) & 1u) << j;
-                zr |= ((z >> seg.lq[j]) & 1u) << j;
-            }
-            const unsigned pt = __popc(tb & z) & 1u;
-            const T cs = mats_s[op.mat];
-            if (x == 0) {
-                pauli_reg_diag(reg, cs.x, cs.y, zr, pt);
-            } else {
-                const int e = (__popc(x & z) + 3) & 3;  // -i * i^{#Y}
-                const float A = e == 0 ? 1.f : e == 2 ? -1.f : 0.f;
-                const float B = e == 1 ? -1.f : e == 3 ? 1.f : 0.f;
-                pauli_reg_dispatch(reg, xr, cs.x, cs.y * A, cs.y * B, -cs.y * B, cs.y * A, zr, pt);
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < kRegAmps; s++) tile[tb | roff[s]] = reg[s];
-        i += 1 + nseg;
-        __syncthreads();
+    for (int i = 0; i < kRegAmps; i++) {
+        if (i) addr = (gray(i) >> gray_flip(i)) & 1 ? addr + d[gray_flip(i)] : addr - d[gray_flip(i)];
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(reg[gray(i)].x), "f"(reg[gray(i)].y)
+                     : "memory");
     }
-    if (vec) {
-        for (unsigned p = threadIdx.x; p < Nt / 2; p += NT) {
-            const unsigned l = p * 2;
-            *reinterpret_cast<uint4 *>(st + (hi_off[l >> L] | (l & Lmask))) =
-                *reinterpret_cast<const uint4 *>(tile + l);
-        }
-    } else {
-        for (unsigned l = threadIdx.x; l < Nt; l += NT) st[hi_off[l >> L] | (l & Lmask)] = tile[l];
+}
+__device__ __forceinline__ void seg_load_smem(float2 *reg, uint32_t addr, const uint32_t *d) {
+#pragma unroll
+    for (int i = 0; i < kRegAmps; i++) {
+        if (i) addr = (gray(i) >> gray_flip(i)) & 1 ? addr + d[gray_flip(i)] : addr - d[gray_flip(i)];
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(reg[gray(i)].x), "=f"(reg[gray(i)].y) : "r"(addr)
+                     : "memory");
     }
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_tile_pass_reg(TileArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_rot_pass(TileArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_pass_body_reg(a, blockIdx.x, smem_raw);
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    float2 *mats_s = tile + (1u << a.m);
+    DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);
+    __shared__ uint32_t bv_s[16];
+    grid_dep_launch_next();
+    const unsigned tid = threadIdx.x, nt = blockDim.x;  // 2^(m-5) threads (NT is the most)
+    for (unsigned i = tid; i < a.n_ops; i += nt) cp_async16(ops_s + i, a.ops + i);
+    {
+        const float2 *gm = reinterpret_cast<const float2 *>(a.mats) + a.mat_first;
+        for (unsigned i = tid; i < a.mat_count; i += nt) cp_async8(mats_s + i, gm + i);
+    }
+    if (tid < 16) bv_s[tid] = (uint32_t)a.bv[tid];  // n <= 32: amplitude indices fit 32 bits
+    const uint32_t bid = blockIdx.x;
+    uint32_t x0 = 0;  // the tile's origin: blockIdx spread over the non-pivot positions
+    for (int j = 0; j < a.n - a.m; j++) x0 |= ((bid >> j) & 1u) << a.ntq[j];
+    cp_async_wait_all();
+    grid_dep_wait();
+    if (a.ctl->status) return;  // a failed assertion earlier on this stream: leave the state
+    __syncthreads();
+    float2 *st = reinterpret_cast<float2 *>(a.state);
+    const uint32_t tile_sa = (uint32_t)__cvta_generic_to_shared(tile);
+    float2 reg[kRegAmps];
+    uint32_t sa_prev = 0, sd_prev[5] = {0, 0, 0, 0, 0};
+    for (uint32_t i = 0; i < a.n_ops;) {
+        const DevOp mk = ops_s[i];  // kSegMarker: lq[0..4] register positions (ascending), flags = #rotations
+        const uint32_t nseg = mk.flags;
+        const bool first = i == 0;
+        const bool last = i + 1 + nseg >= a.n_ops;
+        // this thread's tile index: its bits spread over the non-register positions
+        uint32_t tb = tid;
+#pragma unroll
+        for (int j = 0; j < 5; j++) tb = ins0(tb, mk.lq[j]);
+        uint32_t sd[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) sd[j] = 8u << mk.lq[j];
+        const uint32_t sa = tile_sa + 8u * tb;
+        if (!first) seg_store_smem(reg, sa_prev, sd_prev);  // the previous segment's layout
+        if (!first) __syncthreads();
+        if (first || last) {
+            uint32_t gd[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) gd[j] = bv_s[mk.lq[j]];
+            uint32_t gb = x0;
+            for (int b = 0; b < a.m; b++)
+                if ((tb >> b) & 1u) gb ^= bv_s[b];
+            if (first) {
+#pragma unroll
+                for (int k = 0; k < kRegAmps; k++) {
+                    if (k) gb ^= gd[gray_flip(k)];
+                    reg[gray(k)] = st[gb];
+                }
+            } else {
+                seg_load_smem(reg, sa, sd);
+            }
+            seg_rotations(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
+                          reinterpret_cast<const float *>(mats_s));
+            if (last) {
+                uint32_t g = x0;
+                for (int b = 0; b < a.m; b++)
+                    if ((tb >> b) & 1u) g ^= bv_s[b];
+                const float sc = a.scale;
+#pragma unroll
+                for (int k = 0; k < kRegAmps; k++) {
+                    if (k) g ^= gd[gray_flip(k)];
+                    st[g] = make_float2(sc * reg[gray(k)].x, sc * reg[gray(k)].y);
+                }
+            }
+        } else {
+            seg_load_smem(reg, sa, sd);
+            __syncthreads();  // all reads of this layout before the next one is written
+            seg_rotations(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
+                          reinterpret_cast<const float *>(mats_s));
+        }
+        sa_prev = sa;
+#pragma unroll
+        for (int j = 0; j < 5; j++) sd_prev[j] = sd[j];
+        i += 1 + nseg;
+    }
 }
 
 // One pass of several independent states in one launch: descs[j] covers
@@ -654,7 +703,7 @@ __device__ void run_resident(const Instance &in, T *tile, double *red, int *bcas
         const DevOp op = nxt;
         if (i + 1 < in.n_ops) nxt = load_op(in.ops + i + 1);  // in flight while op runs
         if (op.k) {
-            apply_op<T, NT, KMAX>(tile, n, op, mats, mbuf);
+            apply_op<T, NT, KMAX>(tile, n, op, mats, mbuf, 0u);
             __syncthreads();
             continue;
         }
@@ -916,8 +965,8 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 512, 2>));
     QSIM_ATTR((k_tile_pass<float, 256, 5>));
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
-    QSIM_ATTR(k_tile_pass_reg<256>);
-    QSIM_ATTR(k_tile_pass_reg<512>);
+    QSIM_ATTR(k_rot_pass<256>);
+    QSIM_ATTR(k_rot_pass<512>);
     QSIM_ATTR((k_tile_pass_multi<float, 256, 2>));
     QSIM_ATTR((k_tile_pass_multi<double, 256, 2>));
     QSIM_ATTR((k_tile_pass_multi<float, 512, 2>));
@@ -936,11 +985,11 @@ cudaError_t setup_kernels() {
     return cudaSuccess;
 }
 
-bool make_tile_args(int dtype, void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
-                    uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
-                    const MeasCtl *ctl, TileArgs *out) {
+bool make_tile_args(int dtype, void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
+                    const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
+                    uint32_t mat_count, const MeasCtl *ctl, TileArgs *out) {
     if (n_ops > (uint32_t)kPassOps || mat_count > (uint32_t)kPassMats || m > 15 || n - m > 48 ||
-        m < 1 || m > n)
+        m < 1 || m > n || n > 63)
         return false;
     TileArgs &a = *out;
     std::memset(&a, 0, sizeof(a));
@@ -953,57 +1002,79 @@ bool make_tile_args(int dtype, void *state, int n, int m, uint64_t tile_mask, co
     a.mat_count = mat_count;
     a.n = n;
     a.m = m;
-    int t = 0, u = 0;
-    for (int b = 0; b < n; b++) {
-        if ((tile_mask >> b) & 1ull) {
-            if (t >= 16) return false;
-            a.tq[t++] = (uint8_t)b;
-        } else {
-            a.ntq[u++] = (uint8_t)b;
-        }
+    const uint64_t all = (1ull << n) - 1;
+    if (__builtin_popcountll(pivots & all) != m || (pivots & ~all)) return false;
+    for (int j = 0; j < m; j++) {
+        if (!basis[j] || (basis[j] & ~all)) return false;
+        a.bv[j] = basis[j];
     }
-    if (t != m) return false;
-    // contiguous low qubits of the tile (the coalesced run length), capped at
-    // 128-byte runs; a pass may lack them when its first op needs the room
-    const int low = __builtin_ctzll(~tile_mask);
+    int u = 0;
+    for (int b = 0; b < n; b++)
+        if (!((pivots >> b) & 1ull)) a.ntq[u++] = (uint8_t)b;
+    // contiguous low run of the tile (128-byte rows at most): the leading
+    // basis vectors are the unit vectors of qubits 0.. and no later basis
+    // vector has a bit below them; a pass may lack such a run
     const int cap = dtype == 0 ? 4 : 3;
-    a.L = low < cap ? low : cap;
-    if (a.L > m) a.L = m;
+    int L = 0;
+    while (L < cap && L < m && basis[L] == (1ull << L)) L++;
+    for (; L > 0; L--) {
+        bool ok = true;
+        for (int j = L; j < m; j++)
+            if (basis[j] & ((1ull << L) - 1)) ok = false;
+        if (ok) break;
+    }
+    a.L = L;
     return true;
 }
 
+// Launch with programmatic stream serialization (see grid_dep_wait).
+template <typename Kern>
+cudaError_t launch_dependent(Kern kern, unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                             const TileArgs &a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
-                             uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
-                             uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
-                             cudaStream_t s) {
+                             uint64_t pivots, const uint64_t *basis, const DevOp *ops, uint32_t n_ops,
+                             const void *mats, uint32_t mat_first, uint32_t mat_count,
+                             const MeasCtl *ctl, cudaStream_t s) {
     TileArgs a;
-    if (!make_tile_args(dtype, state, n, m, tile_mask, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
+    if (!make_tile_args(dtype, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
         return cudaErrorInvalidValue;
     const unsigned grid = 1u << (n - m);
     const size_t smem = tile_smem_bytes(dtype, m);
     if (kmax > 2) {
-        if (dtype == 0) k_tile_pass<float, 256, 5><<<grid, 256, smem, s>>>(a);
-        else k_tile_pass<double, 256, 5><<<grid, 256, smem, s>>>(a);
-    } else if (dtype == 0) {
-        if (threads == 512) k_tile_pass<float, 512, 2><<<grid, 512, smem, s>>>(a);
-        else k_tile_pass<float, 256, 2><<<grid, 256, smem, s>>>(a);
-    } else {
-        if (threads == 512) k_tile_pass<double, 512, 2><<<grid, 512, smem, s>>>(a);
-        else k_tile_pass<double, 256, 2><<<grid, 256, smem, s>>>(a);
+        if (dtype == 0) return launch_dependent(k_tile_pass<float, 256, 5>, grid, 256, smem, s, a);
+        return launch_dependent(k_tile_pass<double, 256, 5>, grid, 256, smem, s, a);
     }
-    return cudaGetLastError();
+    if (dtype == 0) {
+        if (threads == 512) return launch_dependent(k_tile_pass<float, 512, 2>, grid, 512, smem, s, a);
+        return launch_dependent(k_tile_pass<float, 256, 2>, grid, 256, smem, s, a);
+    }
+    if (threads == 512) return launch_dependent(k_tile_pass<double, 512, 2>, grid, 512, smem, s, a);
+    return launch_dependent(k_tile_pass<double, 256, 2>, grid, 256, smem, s, a);
 }
 
-cudaError_t launch_tile_pass_reg(void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
-                                 uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
-                                 const MeasCtl *ctl, cudaStream_t s) {
-    if (m < 10 || m > 14) return cudaErrorInvalidValue;
+cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
+                            const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
+                            uint32_t mat_count, float scale, const MeasCtl *ctl, cudaStream_t s) {
+    if (m < 10 || m > 14 || n > 32) return cudaErrorInvalidValue;
     TileArgs a;
-    if (!make_tile_args(0, state, n, m, tile_mask, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
+    if (!make_tile_args(0, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
         return cudaErrorInvalidValue;
-    if (m <= 13) k_tile_pass_reg<256><<<1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s>>>(a);
-    else k_tile_pass_reg<512><<<1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s>>>(a);
-    return cudaGetLastError();
+    a.scale = scale;
+    if (m <= 13) return launch_dependent(k_rot_pass<256>, 1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s, a);
+    return launch_dependent(k_rot_pass<512>, 1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s, a);
 }
 
 cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,

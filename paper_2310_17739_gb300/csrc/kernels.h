@@ -12,7 +12,12 @@ namespace qsim {
 // One instruction of a device program (16 bytes).  k > 0: dense 2^k x 2^k
 // complex matrix at mats[mat] (row-major), bit j of the local matrix index
 // <-> tile position lq[j].  k == 0: event `ev` (1 measure, 2 reset) on global
-// qubit lq[0], flags bit 0 = assertion mode.
+// qubit lq[0], flags bit 0 = assertion mode.  k == 7: Pauli rotation in tile
+// coordinates: X mask lq[0..1], Z mask lq[2..3], lq[4] bit 0 = odd (the pair
+// factor is i W rather than W), Z parity mask over the tile origin's bits in
+// flags | pad << 16, coefficient (cos theta, W) at mats[mat]:
+//   a'_j = cos a_j + W (odd ? i : 1) (-1)^{parity(k & z) ^ parity(zc & tile)} a_k,  k = j ^ x.
+// Inside a register segment a rotation is a RegRot instead.
 struct DevOp {
     uint8_t k;
     uint8_t ev;
@@ -101,21 +106,48 @@ struct TileArgs {
     int L;
     uint32_t cta_first;  // multi-state launches: first block of this state's pass
     uint32_t pad;
-    uint8_t tq[16];      // tile qubits, ascending (m entries)
-    uint8_t ntq[48];     // other qubits, ascending (n - m entries)
+    float scale;         // register-segment passes: factor applied when the tile is written back
+    uint32_t pad2;
+    uint64_t bv[16];     // tile basis: tile bit j <-> amplitude-index XOR bv[j] (m entries)
+    uint8_t ntq[48];     // non-pivot qubits, ascending (n - m entries): the tile origin's bits
 };
-// Fill a TileArgs for a pass over tile_mask (returns false if it cannot run).
-bool make_tile_args(int dtype, void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
-                    uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
-                    const MeasCtl *ctl, TileArgs *out);
+// Fill a TileArgs for a pass whose tile subspace has pivot positions
+// `pivots` and basis vectors basis[0..m) (returns false if it cannot run).
+bool make_tile_args(int dtype, void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
+                    const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
+                    uint32_t mat_count, const MeasCtl *ctl, TileArgs *out);
 // A complex64 pass of rotations laid out in register segments (see
-// kSegMarker): 2^(m-5) threads, 32 amplitudes each; 10 <= m <= 14.
-cudaError_t launch_tile_pass_reg(void *state, int n, int m, uint64_t tile_mask, const DevOp *ops,
-                                 uint32_t n_ops, const void *mats, uint32_t mat_first, uint32_t mat_count,
-                                 const MeasCtl *ctl, cudaStream_t s);
+// kSegMarker): 2^(m-5) threads, 32 amplitudes each; 10 <= m <= 14, n <= 32.
+// Its rotations carry (cos, t = W / cos) and run as a' = a + t (...) with the
+// cosines' product `scale` applied when the tile is written back.
+cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
+                            const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
+                            uint32_t mat_count, float scale, const MeasCtl *ctl, cudaStream_t s);
 // Op-size marker of a register segment: lq[0..4] = the 5 tile positions held
 // in registers, flags = number of rotations that follow in the segment.
 constexpr uint8_t kSegMarker = 8;
+// A rotation inside a register segment (the 16 bytes of a DevOp slot).  sel =
+// xr << 1 | odd, xr its X mask over the segment's 5 register slots; zt its
+// tile-local Z mask; zc as in DevOp; tab = offset (in floats, a multiple of
+// 4) of its coefficient table in the pass's coefficient slice.  The table
+// lists u_p = t (-1)^{parity(j_p & zr)}, t = W / cos theta, zr the Z mask over
+// the register slots, for the pairs p = 0..15 (j_p = p with a zero inserted
+// at xr's top bit; for xr = 0, the 32 slots), followed by the same values
+// negated; a thread takes the negated half when parity(zt & tb) ^
+// parity(zc & tile) = 1.  Then, for the pairs (j, k = j ^ xr):
+//   odd:  a'_j = a_j + i u a_k,  a'_k = a_k + i u a_j
+//   even: a'_j = a_j - u a_k,    a'_k = a_k + u a_j
+// (xr = 0: a'_j = (1 + u (odd ? i : 1)) a_j), and the cosines multiply the
+// tile when it is written back.
+struct RegRot {
+    uint8_t k;  // kPauli
+    uint8_t sel;
+    uint16_t zt;
+    uint32_t tab;
+    uint32_t zc;
+    uint32_t pad;
+};
+static_assert(sizeof(RegRot) == sizeof(DevOp), "RegRot layout");
 // Several states' passes in one launch: descs[0..n_desc) in device memory with
 // increasing cta_first; total_ctas blocks; max_m the largest tile among them.
 cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,
@@ -131,9 +163,9 @@ size_t tile_smem_bytes(int dtype, int m);
 // mat_first + mat_count) (op.mat relative to mat_first).  kmax: largest dense
 // op (qubits); <= 2 selects the register-lean build without k >= 3 paths.
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
-                             uint64_t tile_mask, const DevOp *ops, uint32_t n_ops, const void *mats,
-                             uint32_t mat_first, uint32_t mat_count, const MeasCtl *ctl,
-                             cudaStream_t s);
+                             uint64_t pivots, const uint64_t *basis, const DevOp *ops, uint32_t n_ops,
+                             const void *mats, uint32_t mat_first, uint32_t mat_count,
+                             const MeasCtl *ctl, cudaStream_t s);
 // Resident whole-state interpreter; kmax as for launch_tile_pass.  The batch
 // form runs one block per instance, shared memory sized for max_n qubits.
 cudaError_t launch_resident(int dtype, int kmax, const Instance &inst, cudaStream_t s);

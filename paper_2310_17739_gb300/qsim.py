@@ -102,7 +102,7 @@ _SIGS = {
     "qsim_status_string": ([_i32], ctypes.c_char_p),
     "qsim_fuse": ([_i32, _i32, _vp, _sz, _vp, _sz, ctypes.POINTER(QsimConfig), _vp, _vp, _vp, _sz, _vp, _sz,
                    ctypes.POINTER(_sz), ctypes.POINTER(_sz)], _i32),
-    "qsim_schedule": ([_i32, _i32, _vp, _sz, _vp, _sz, ctypes.POINTER(QsimConfig), _vp, _vp, _vp, _sz,
+    "qsim_schedule": ([_i32, _i32, _vp, _sz, _vp, _sz, ctypes.POINTER(QsimConfig), _vp, _vp, _vp, _vp, _sz,
                        ctypes.POINTER(_sz)], _i32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -486,7 +486,9 @@ class Server:
 
 # ----------------------------------------------------- host-only inspection --
 def fuse(n, gates, mats=None, dtype=C64, **cfg):
-    """Compiled op list of one chunk: list of (k, qubits, matrix) / ('event', op, q, flags)."""
+    """Compiled op list of one chunk: list of (k, qubits, matrix) / ('event', op, q, flags)
+    / ('pauli', x, z, theta) for exp(-i theta P) / ('frame', x, z, g) for
+    i^g exp(-i pi/2 P), with P = i^{|x & z|} X^x Z^z."""
     g = _gates(gates)
     m = _mats(mats)
     c = make_config(**cfg)
@@ -510,8 +512,12 @@ def fuse(n, gates, mats=None, dtype=C64, **cfg):
         elif k == PAULI_K:
             xm = int(oq[6 * i]) | (int(oq[6 * i + 1]) << 32)
             zm = int(oq[6 * i + 2]) | (int(oq[6 * i + 3]) << 32)
+            fl = int(oq[6 * i + 4])
             off = int(om[i])
-            out.append(("pauli", xm, zm, float(np.arctan2(md[off + 1], md[off]))))
+            if fl & 4:  # Pauli-frame flush: i^g exp(-i pi/2 P)
+                out.append(("frame", xm, zm, fl & 3))
+            else:
+                out.append(("pauli", xm, zm, float(np.arctan2(md[off + 1], md[off]))))
         else:
             d = 1 << k
             off = int(om[i])
@@ -520,18 +526,23 @@ def fuse(n, gates, mats=None, dtype=C64, **cfg):
     return out
 
 
-def schedule(n, gates, mats=None, dtype=C64, **cfg):
-    """Pass table of one chunk: list of (tile_mask, first, count)."""
+def schedule(n, gates, mats=None, dtype=C64, with_basis=False, **cfg):
+    """Pass table of one chunk: list of (pivot_mask, first, count), or with
+    with_basis=True (pivot_mask, first, count, basis_vectors)."""
     g = _gates(gates)
     m = _mats(mats)
     c = make_config(**cfg)
     npass = ctypes.c_size_t()
-    _lib.qsim_schedule(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), None, None, None, 0,
+    _lib.qsim_schedule(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), None, None, None, None, 0,
                        ctypes.byref(npass))
     K = max(npass.value, 1)
     t = np.zeros(K, dtype=np.uint64)
     f = np.zeros(K, dtype=np.uint64)
     cnt = np.zeros(K, dtype=np.uint32)
+    b = np.zeros(16 * K, dtype=np.uint64)
     _check(_lib.qsim_schedule(n, dtype, _ptr(g), g.size, _ptr(m), m.size, ctypes.byref(c), _ptr(t), _ptr(f),
-                              _ptr(cnt), K, ctypes.byref(npass)))
+                              _ptr(cnt), _ptr(b), K, ctypes.byref(npass)))
+    if with_basis:
+        return [(int(t[i]), int(f[i]), int(cnt[i]), [int(v) for v in b[16 * i: 16 * i + 16] if v])
+                for i in range(npass.value)]
     return [(int(t[i]), int(f[i]), int(cnt[i])) for i in range(npass.value)]

@@ -169,6 +169,118 @@ def test_schedule_invariants(dtype, tile_bits):
     assert len(m_seen) == 1
 
 
+def _span_contains(basis, v):
+    """GF(2) membership of v in the span of basis (Gaussian elimination)."""
+    rows = []
+    for b in basis:
+        for r in rows:
+            if b & (r & -r):
+                b ^= r
+        if b:
+            rows.append(b)
+    assert len(rows) == len(basis), "basis vectors are not independent"
+    for r in rows:
+        if v & (r & -r):
+            v ^= r
+    return v == 0
+
+
+@pytest.mark.parametrize("dtype,tile_bits,fusion", [(0, 0, 2), (0, 10, 2), (1, 9, 2), (0, 9, 1)])
+def test_subspace_schedule_invariants(dtype, tile_bits, fusion):
+    """Every pass's tile is an m-dimensional subspace that holds each dense
+    op's qubit unit vectors and each rotation's X mask; the forced low qubits
+    lead the basis; the pivots are m distinct positions."""
+    n = 16
+    c = W.ucc_circuit(n, seed=11, n_gadgets=120, w_lo=2, w_hi=8, target_gates=8000, n_meas=4)
+    ops = qs.fuse(n, c.gates, dtype=dtype, fusion=fusion, tile_bits=tile_bits)
+    passes = qs.schedule(n, c.gates, dtype=dtype, fusion=fusion, tile_bits=tile_bits, with_basis=True)
+    L = 4 if dtype == 0 else 3
+    covered = 0
+    for tile, first, count, basis in passes:
+        assert first == covered
+        covered += count
+        if tile == 0:
+            assert count == 1 and ops[first][0] == "event"
+            continue
+        m = bin(tile).count("1")
+        assert len(basis) == m
+        assert basis[:L] == [1 << b for b in range(L)]
+        for o in ops[first: first + count]:
+            if o[0] in ("pauli", "frame"):
+                assert _span_contains(basis, o[1])
+            else:
+                for q in o[1]:
+                    assert _span_contains(basis, 1 << q)
+        if fusion == 1:
+            assert sorted(basis) == [1 << b for b in range(n) if (tile >> b) & 1]
+    assert covered == len(ops)
+
+
+def test_subspace_tiles_hold_more_rotations_per_pass():
+    """A rotation costs one tile dimension (its X mask), not one per qubit:
+    a 14-dimensional tile takes about ten rotations of weight 2-6 on 21 qubits."""
+    n = 21
+    c = W.ucc_circuit(n, seed=3, n_gadgets=400, w_lo=2, w_hi=6, target_gates=30000)
+    passes = qs.schedule(n, c.gates, dtype=qs.C64, fusion=2, tile_bits=14)
+    rot = sum(cnt for t, f, cnt in passes if t)
+    assert rot / len(passes) >= 9.0
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pauli_frame_keeps_cosines_large_and_flushes_before_events(seed):
+    """Fusion level 2 splits every rotation with |cos| < |sin| into a Pauli
+    (kept in a frame) and a rotation with |cos| >= 1/sqrt(2); the frame is
+    applied before each measurement and at the end, so the op list is still
+    exactly the circuit."""
+    n = 9
+    c = W.ucc_circuit(n, seed=seed, n_gadgets=40, w_lo=2, w_hi=6, theta="uniform", target_gates=3000,
+                      n_meas=3)
+    ops = qs.fuse(n, c.gates, dtype=qs.C128, fusion=2, tile_bits=7)
+    rot = [o for o in ops if o[0] == "pauli"]
+    assert rot and all(abs(np.cos(o[3])) >= np.sqrt(0.5) - 1e-12 for o in rot)
+    assert any(o[0] == "frame" for o in ops)
+    # segment by segment against the oracle: the state each measurement sees
+    # is the circuit's own (the frame was flushed), and so is the final one
+    meas_at = [i for i in range(c.G) if int(c.gates[i]["op"]) == OP["MEASURE"]]
+    psi = oracle.basis_state(n)
+    ref = oracle.basis_state(n)
+    r = oracle.run(ref, n, c.gates, seed=5)
+    seg, k = [], 0
+    for o in ops + [("event", -1, -1, -1)]:
+        if o[0] == "event":
+            psi = apply_compiled(psi, n, seg)
+            seg = []
+            if o[1] == -1:
+                break
+            before = oracle.basis_state(n)
+            oracle.run(before, n, c.gates[: meas_at[k]], seed=5)
+            assert np.abs(psi - before).max() < 1e-11
+            st, out, pr = oracle.measure(psi, n, o[2], seed=5, k=k)
+            assert out == r.outcomes[k]
+            k += 1
+        else:
+            seg.append(o)
+    assert np.abs(psi - ref).max() < 1e-11
+
+
+def test_pauli_frame_conjugates_dense_ops():
+    """Dense ops between split rotations reach the state conjugated by the frame."""
+    n = 7
+    rng = np.random.default_rng(4)
+    pieces = []
+    for blk in range(12):
+        s, L = W.random_pauli(rng, n, 2, 4)
+        pieces.append(W.gadget(s, L, float(rng.uniform(0.9, 2.2))))   # |cos| < |sin|: split
+        pieces.append(W.random_circuit(n, 6, seed=100 + blk, with_generic=False).gates)
+    g = np.concatenate(pieces)
+    ops = qs.fuse(n, g, dtype=qs.C128, fusion=2, tile_bits=7)
+    assert any(o[0] == "frame" for o in ops)
+    psi = W.random_state(n, seed=8)
+    ref = psi.copy()
+    oracle.run(ref, n, g)
+    assert np.abs(apply_compiled(psi, n, ops) - ref).max() < 1e-12
+
+
 def test_invalid_records_rejected_on_host():
     n = 4
     bad = [W.records([(OP["H"], 4, 0, 0, 0, 0)]), W.records([(OP["CX"], 2, 2, 0, 0, 0)]),
@@ -189,6 +301,9 @@ def apply_compiled(psi, n, ops):
             _, x, z, t = o
             P = H.term_dense(n, x, z)
             psi = np.cos(t) * psi - 1j * np.sin(t) * (P @ psi)
+        elif o[0] == "frame":  # i^g exp(-i pi/2 P) = i^g (-i) P
+            _, x, z, g = o
+            psi = (1j) ** g * (-1j) * (H.term_dense(n, x, z) @ psi)
         elif o[0] == "event":
             raise AssertionError("events are not applied here")
         else:
@@ -205,7 +320,7 @@ def test_gadgets_become_pauli_rotations(seed, k_max):
     ops = qs.fuse(n, c.gates, dtype=qs.C128, fusion=2, k_max=k_max, tile_bits=8)
     n_pauli = sum(1 for o in ops if o[0] == "pauli")
     assert n_pauli == c.meta["n_gadgets_total"]          # every gadget recognised
-    assert all(o[0] == "pauli" for o in ops)
+    assert all(o[0] in ("pauli", "frame") for o in ops)
     psi = W.random_state(n, seed=seed)
     ref = psi.copy()
     oracle.run(ref, n, c.gates)

@@ -46,6 +46,8 @@ def parse():
                     help="gate count of the circuit (the named workload is 115,000,000)")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--k-max", type=int, default=2)
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
+                    help="with --fusion >= 0: resident-block rotation passes")
     ap.add_argument("--fusion", type=int, default=-1,
                     help="-1: autotune (paper fusion, k-qubit merge, Pauli-gadget rotations); "
                          "0/1/2 force a fusion level")
@@ -215,7 +217,8 @@ def run_ours(args):
         sweep = [dict(config=r["config"], gates_per_s=r["gates_per_s"], passes=r["passes"],
                       fused_ops=r["fused_ops"]) for r in entry["report"]]
     else:
-        cfg = dict(fusion=args.fusion, k_max=args.k_max, tile_bits=args.tile_bits or 13)
+        cfg = dict(fusion=args.fusion, k_max=args.k_max, tile_bits=args.tile_bits or 13,
+                   persistent=args.persistent)
     stream = torch.cuda.current_stream()
     sim = qs.Sim(n, "c64", stream=stream, config=cfg, seed=1003)
     t0 = time.perf_counter()

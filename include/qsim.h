@@ -116,18 +116,29 @@ typedef struct {
 
 /* ------------------------------------------------------------- compiling --
  * fusion   0: no fusion (one C1/C2 op per gate, still tiled into passes);
- *          1: the paper's four fusion stages (C1/C2 only).
+ *          1: the paper's four fusion stages (C1/C2 only);
+ *          2: stages 1-4 plus Pauli-gadget recognition: a basis change, a CX
+ *          network computing a parity, RZ, the network reversed and the
+ *          basis undone become one rotation exp(-i theta P), kept with a
+ *          Pauli frame (rotations with |cos| < |sin| are split, their Pauli
+ *          factor folded into the frame, which is applied before every
+ *          measurement or reset and at the end of the stream).
  * k_max    2: the paper's C1/C2 ops; 3..5: fused ops of a pass are further
  *          merged into dense 2^k x 2^k blocks of up to k_max qubits when the
  *          cost model says it is cheaper.
- * tile_bits m: qubits per shared-memory tile (pass); 0 picks by dtype and n.
- *          States with n <= tile limit run resident in one block.
- * threads  threads per block; 0 = 256.
+ * tile_bits m: dimension of a pass's tile (see qsim_schedule); 0 picks by
+ *          dtype and n.  States with n <= tile limit run resident in one block.
+ * threads  threads per block of the generic tile pass (256 or 512); 0 = auto,
+ *          which also lets complex64 rotation passes run as register segments
+ *          (2^(m-5) threads of 32 amplitudes).
  * chunk_gates  qsim_apply compiles and launches the stream in chunks of this
  *          many gates, overlapping host compilation with device work; 0 = 2^20.
  * lookahead  how many fused ops the pass scheduler may scan past an op that
  *          does not fit, pulling later ops on disjoint qubits forward; 0 = 64.
  * compile_threads  host threads compiling chunks ahead of the launcher; 0 = auto.
+ * persistent  1: register-segment rotation passes (m <= 13) run as resident
+ *          blocks that take tiles from a device counter and prefetch the next
+ *          tile while computing the current one; 0: one block per tile.
  */
 typedef struct {
     int32_t fusion;
@@ -137,7 +148,7 @@ typedef struct {
     int32_t chunk_gates;
     int32_t lookahead;
     int32_t compile_threads;
-    int32_t reserved;
+    int32_t persistent;
 } qsim_config;
 
 typedef struct {

@@ -354,6 +354,8 @@ struct qsim_ctx {
     size_t log_cap = 0;
     uint64_t log_n = 0;
     double *partials = nullptr;
+    unsigned long long *tile_ctr = nullptr;  // persistent rotation passes: tile counter
+    unsigned long long tile_base = 0;        // its value when the next such pass starts
     size_t partials_cap = 0;  // doubles
     uint64_t ordinal = 0;
     uint64_t seed = 0;
@@ -600,7 +602,20 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
                             c->prof_used < c->prof_ev.size();
         if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
         const uint64_t *basis = dc.bvec.data() + p.basis;
-        if (p.reg)
+        if (p.reg && c->cfg.persistent && dc.m <= 13) {
+            if (!c->tile_ctr) {
+                c->tile_ctr = (unsigned long long *)dalloc(c, sizeof(unsigned long long));
+                if (!c->tile_ctr) return fail(c, QSIM_E_OOM, "tile counter allocation failed");
+                CK(cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "tile counter");
+                c->tile_base = 0;
+            }
+            uint32_t grid = 0;
+            CK(qsim::launch_rot_pipe(c->state, c->n, dc.m, p.tile, basis, dc.d_ops + p.first, p.count,
+                                     dc.d_mats, (uint32_t)p.mat_first, p.mat_count, p.scale, c->ctl,
+                                     c->tile_ctr, c->tile_base, &grid, c->stream),
+               "persistent rotation pass launch");
+            c->tile_base += (1ull << (c->n - dc.m)) + grid;
+        } else if (p.reg)
             CK(qsim::launch_rot_pass(c->state, c->n, dc.m, p.tile, basis, dc.d_ops + p.first, p.count,
                                      dc.d_mats, (uint32_t)p.mat_first, p.mat_count, p.scale, c->ctl,
                                      c->stream),
@@ -790,6 +805,7 @@ qsim_status qsim_destroy(qsim_ctx *c) {
     dfree(c, c->ctl, sizeof(MeasCtl));
     dfree(c, c->log, c->log_cap * sizeof(MeasRec));
     dfree(c, c->partials, c->partials_cap * sizeof(double));
+    dfree(c, c->tile_ctr, sizeof(unsigned long long));
     cudaStreamSynchronize(c->stream);
     for (auto &s : c->staging) {
         cudaEventDestroy(s.done);
@@ -828,6 +844,7 @@ qsim_status qsim_set_config(qsim_ctx *c, const qsim_config *cfg) {
         return fail(c, QSIM_E_INVAL, "threads must be 0, 256 or 512");
     if (cfg->chunk_gates < 0 || cfg->lookahead < 0 || cfg->compile_threads < 0)
         return fail(c, QSIM_E_INVAL, "negative size");
+    if (cfg->persistent != 0 && cfg->persistent != 1) return fail(c, QSIM_E_INVAL, "persistent must be 0 or 1");
     c->cfg = qsim::config_from(cfg);
     return QSIM_OK;
 }
@@ -1747,6 +1764,7 @@ void ctx_free_async(qsim_ctx *c) {
     dfree(c, c->ctl, sizeof(MeasCtl));
     dfree(c, c->log, c->log_cap * sizeof(MeasRec));
     dfree(c, c->partials, c->partials_cap * sizeof(double));
+    dfree(c, c->tile_ctr, sizeof(unsigned long long));
     for (auto &s : c->staging) {
         cudaEventSynchronize(s.done);
         cudaEventDestroy(s.done);

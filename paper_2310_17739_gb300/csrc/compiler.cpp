@@ -387,6 +387,7 @@ Config config_from(const qsim_config *c) {
     k.chunk_gates = c->chunk_gates;
     k.lookahead = c->lookahead;
     k.compile_threads = c->compile_threads;
+    k.persistent = c->persistent;
     return k;
 }
 
@@ -399,6 +400,7 @@ void config_to(const Config &c, qsim_config *o) {
     o->chunk_gates = c.chunk_gates;
     o->lookahead = c.lookahead;
     o->compile_threads = c.compile_threads;
+    o->persistent = c.persistent;
 }
 
 static int max_tile_bits(qsim_dtype dt) { return dt == QSIM_C64 ? 14 : 13; }

@@ -150,6 +150,7 @@ struct Config {
     int chunk_gates = 0;
     int lookahead = 0;
     int compile_threads = 0;
+    int persistent = 0;
 };
 
 Config config_from(const qsim_config *c);

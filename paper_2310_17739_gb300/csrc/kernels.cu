@@ -20,6 +20,7 @@
 // Every wait in this file is a __syncthreads; no kernel spins on memory.
 #include "kernels.h"
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -476,13 +477,21 @@ __host__ __device__ constexpr int pair_lo(int p, int H) {  // p with a zero inse
 template <int XR, bool ODD>
 __device__ __forceinline__ void rot_reg(float2 *a, const float4 *U) {
     constexpr int H = top_bit(XR);
+    float u[16];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float4 v = U[q];
+        u[4 * q] = v.x;
+        u[4 * q + 1] = v.y;
+        u[4 * q + 2] = v.z;
+        u[4 * q + 3] = v.w;
+    }
 #pragma unroll
     for (int p = 0; p < 16; p++) {
         const int j = pair_lo(p, H);
         const int k = j ^ XR;
         const float2 aj = a[j], ak = a[k];
-        const float4 v = U[p >> 2];
-        const float uj = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+        const float uj = u[p];
         if (ODD) {
             a[j] = make_float2(fmaf(-uj, ak.y, aj.x), fmaf(uj, ak.x, aj.y));
             a[k] = make_float2(fmaf(-uj, aj.y, ak.x), fmaf(uj, aj.x, ak.y));
@@ -647,6 +656,154 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_rot_pass(TileArgs a) 
         for (int j = 0; j < 5; j++) sd_prev[j] = sd[j];
         i += 1 + nseg;
     }
+}
+
+// ------------------------------------------------ persistent rotation pass --
+// The same register-segment pass, run by blocks that stay resident and take
+// tiles from a device counter: tile k + 1 of a block is copied into shared
+// memory (cp.async, whole 128-byte rows) while tile k is computed in
+// registers, so the L2 traffic of one tile overlaps the arithmetic of the
+// previous one, and blocks on lightly loaded SMs take more tiles.  Tiles are
+// numbered base, base + 1, ... on the counter: a block stops at the first
+// number past the pass's last tile, so each launch advances the counter by
+// exactly n_tiles + gridDim.x.  Needs the 4 forced low qubits (whole rows).
+constexpr int kMaxRows = 1024;  // 2^(m-4) rows, m <= 14
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT <= 64 ? 8 : NT <= 128 ? 4 : 2)
+    k_rot_pipe(TileArgs a, unsigned long long *ctr, unsigned long long base, uint32_t n_tiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned Nt = 1u << a.m;
+    float2 *bufs = reinterpret_cast<float2 *>(smem_raw);  // two tiles, then the program slices
+    float2 *mats_s = bufs + 2 * Nt;
+    DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + ((a.mat_count + 1) & ~1u));
+    __shared__ uint32_t bv_s[16];
+    __shared__ uint32_t rowL[kMaxRows];   // XOR of the basis vectors of a row's local bits 4..m-1
+    __shared__ uint32_t next_tile[2];
+    grid_dep_launch_next();
+    const unsigned tid = threadIdx.x, nt = blockDim.x;
+    for (unsigned i = tid; i < a.n_ops; i += nt) cp_async16(ops_s + i, a.ops + i);
+    {
+        const float2 *gm = reinterpret_cast<const float2 *>(a.mats) + a.mat_first;
+        for (unsigned i = tid; i < a.mat_count; i += nt) cp_async8(mats_s + i, gm + i);
+    }
+    if (tid < 16) bv_s[tid] = (uint32_t)a.bv[tid];
+    const unsigned rows = Nt >> 4;
+    for (unsigned r = tid; r < rows; r += nt) {
+        uint32_t v = 0;
+        for (int j = 0; j < a.m - 4; j++)
+            if ((r >> j) & 1u) v ^= (uint32_t)a.bv[4 + j];
+        rowL[r] = v;
+    }
+    cp_async_wait_all();
+    grid_dep_wait();
+    if (a.ctl->status) {  // a failed assertion earlier on this stream: leave the state, keep the count
+        if (tid == 0)
+            while (atomicAdd(ctr, 1ull) - base < n_tiles) {
+            }
+        return;
+    }
+    if (tid == 0) {
+        next_tile[0] = (uint32_t)min(atomicAdd(ctr, 1ull) - base, (unsigned long long)n_tiles);
+        next_tile[1] = next_tile[0] < n_tiles ? (uint32_t)min(atomicAdd(ctr, 1ull) - base, (unsigned long long)n_tiles)
+                                              : n_tiles;
+    }
+    __syncthreads();
+    float2 *st = reinterpret_cast<float2 *>(a.state);
+    // the tile's origin: its number spread over the non-pivot positions
+    auto origin = [&](uint32_t t) {
+        uint32_t x0 = 0;
+        for (int j = 0; j < a.n - a.m; j++) x0 |= ((t >> j) & 1u) << a.ntq[j];
+        return x0;
+    };
+    // copy tile t into buf as whole rows in address order
+    auto prefetch = [&](uint32_t t, float2 *buf) {
+        const uint32_t x0 = origin(t);
+        for (unsigned c = tid; c < Nt / 2; c += nt) {  // 16-byte chunks, 8 per row
+            const unsigned r = c >> 3;
+            const uint32_t row = (x0 ^ rowL[r]) & ~15u;
+            cp_async16(buf + 2 * c, st + row + 2 * (c & 7));
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    uint32_t cur = next_tile[0];
+    if (cur < n_tiles) prefetch(cur, bufs);
+    float2 reg[kRegAmps];
+    for (uint32_t k = 0; cur < n_tiles; k++) {
+        float2 *buf = bufs + (k & 1) * Nt;
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();  // tile k in place; the other buffer's last readers are done
+        const uint32_t nxt = next_tile[(k + 1) & 1];
+        if (tid == 0 && nxt < n_tiles)
+            next_tile[k & 1] = (uint32_t)min(atomicAdd(ctr, 1ull) - base, (unsigned long long)n_tiles);
+        if (nxt < n_tiles) prefetch(nxt, bufs + ((k + 1) & 1) * Nt);
+        const uint32_t bid = cur;
+        const uint32_t x0 = origin(cur);
+        const uint32_t tile_sa = (uint32_t)__cvta_generic_to_shared(buf);
+        uint32_t sa_prev = 0, sd_prev[5] = {0, 0, 0, 0, 0};
+        for (uint32_t i = 0; i < a.n_ops;) {
+            const DevOp mk = ops_s[i];
+            const uint32_t nseg = mk.flags;
+            const bool first = i == 0;
+            const bool last = i + 1 + nseg >= a.n_ops;
+            uint32_t tb = tid;
+#pragma unroll
+            for (int j = 0; j < 5; j++) tb = ins0(tb, mk.lq[j]);
+            uint32_t sd[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) sd[j] = 8u << mk.lq[j];
+            const uint32_t sa = tile_sa + 8u * tb;
+            if (first) {
+                // rows sit in address order: local index l at l ^ (rowL[l >> 4] & 15)
+                uint32_t pd[5];
+#pragma unroll
+                for (int j = 0; j < 5; j++) {
+                    const uint32_t u = 1u << mk.lq[j];
+                    pd[j] = 8u * (u ^ (u >= 16 ? bv_s[mk.lq[j]] & 15u : 0u));
+                }
+                uint32_t tphys = tb;
+                for (int b = 4; b < a.m; b++)
+                    if ((tb >> b) & 1u) tphys ^= bv_s[b] & 15u;
+                uint32_t off = 8u * tphys;
+#pragma unroll
+                for (int q = 0; q < kRegAmps; q++) {
+                    if (q) off ^= pd[gray_flip(q)];
+                    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                                 : "=f"(reg[gray(q)].x), "=f"(reg[gray(q)].y)
+                                 : "r"(tile_sa + off)
+                                 : "memory");
+                }
+                if (!last) __syncthreads();  // every first-layout read before the tile is re-laid out
+            } else {
+                seg_store_smem(reg, sa_prev, sd_prev);
+                __syncthreads();
+                seg_load_smem(reg, sa, sd);
+                if (!last) __syncthreads();
+            }
+            seg_rotations(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
+                          reinterpret_cast<const float *>(mats_s));
+            if (last) {
+                uint32_t gd[5];
+#pragma unroll
+                for (int j = 0; j < 5; j++) gd[j] = bv_s[mk.lq[j]];
+                uint32_t g = x0;
+                for (int b = 0; b < a.m; b++)
+                    if ((tb >> b) & 1u) g ^= bv_s[b];
+                const float sc = a.scale;
+#pragma unroll
+                for (int q = 0; q < kRegAmps; q++) {
+                    if (q) g ^= gd[gray_flip(q)];
+                    st[g] = make_float2(sc * reg[gray(q)].x, sc * reg[gray(q)].y);
+                }
+            }
+            sa_prev = sa;
+#pragma unroll
+            for (int j = 0; j < 5; j++) sd_prev[j] = sd[j];
+            i += 1 + nseg;
+        }
+        cur = nxt;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // One pass of several independent states in one launch: descs[j] covers
@@ -967,6 +1124,9 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
     QSIM_ATTR(k_rot_pass<256>);
     QSIM_ATTR(k_rot_pass<512>);
+    QSIM_ATTR(k_rot_pipe<64>);
+    QSIM_ATTR(k_rot_pipe<128>);
+    QSIM_ATTR(k_rot_pipe<256>);
     QSIM_ATTR((k_tile_pass_multi<float, 256, 2>));
     QSIM_ATTR((k_tile_pass_multi<double, 256, 2>));
     QSIM_ATTR((k_tile_pass_multi<float, 512, 2>));
@@ -1075,6 +1235,42 @@ cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const ui
     a.scale = scale;
     if (m <= 13) return launch_dependent(k_rot_pass<256>, 1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s, a);
     return launch_dependent(k_rot_pass<512>, 1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s, a);
+}
+
+cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
+                            const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
+                            uint32_t mat_count, float scale, const MeasCtl *ctl, unsigned long long *ctr,
+                            unsigned long long base, uint32_t *grid_used, cudaStream_t s) {
+    if (m < 10 || m > 13 || n > 32) return cudaErrorInvalidValue;
+    TileArgs a;
+    if (!make_tile_args(0, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
+        return cudaErrorInvalidValue;
+    for (int j = 0; j < 4; j++)  // whole 128-byte rows
+        if (basis[j] != (1ull << j)) return cudaErrorInvalidValue;
+    a.scale = scale;
+    const size_t smem = ((size_t)16 << m) + 8 * (size_t)((mat_count + 1) & ~1u) + sizeof(DevOp) * n_ops;
+    // resident blocks per SM: shared memory (this launch's plus the static
+    // 4.1 KB) and registers (128 per thread)
+    const unsigned threads = 1u << (m - 5);
+    int per_sm = (int)((227u * 1024u) / (smem + 4352));
+    per_sm = std::min(per_sm, (int)(512u / threads));
+    per_sm = std::max(per_sm, 1);
+    const uint32_t n_tiles = 1u << (n - m);
+    const uint32_t grid = std::min<uint32_t>(n_tiles, 152u * (uint32_t)per_sm);
+    *grid_used = grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (m <= 11) return cudaLaunchKernelEx(&cfg, k_rot_pipe<64>, a, ctr, base, n_tiles);
+    if (m == 12) return cudaLaunchKernelEx(&cfg, k_rot_pipe<128>, a, ctr, base, n_tiles);
+    return cudaLaunchKernelEx(&cfg, k_rot_pipe<256>, a, ctr, base, n_tiles);
 }
 
 cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,

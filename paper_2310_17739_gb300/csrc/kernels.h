@@ -123,6 +123,15 @@ bool make_tile_args(int dtype, void *state, int n, int m, uint64_t pivots, const
 cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
                             const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
                             uint32_t mat_count, float scale, const MeasCtl *ctl, cudaStream_t s);
+// The same pass with resident blocks taking tiles from the device counter
+// *ctr (numbers base .. base + 2^(n-m) - 1 are this pass's tiles), each
+// prefetching its next tile while it computes the current one.  A launch
+// advances the counter by exactly 2^(n-m) + *grid_used.  10 <= m <= 13,
+// n <= 32, and the basis must start with the unit vectors of qubits 0..3.
+cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
+                            const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
+                            uint32_t mat_count, float scale, const MeasCtl *ctl, unsigned long long *ctr,
+                            unsigned long long base, uint32_t *grid_used, cudaStream_t s);
 // Op-size marker of a register segment: lq[0..4] = the 5 tile positions held
 // in registers, flags = number of rotations that follow in the segment.
 constexpr uint8_t kSegMarker = 8;

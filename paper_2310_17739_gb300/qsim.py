@@ -36,7 +36,7 @@ class QsimConfig(ctypes.Structure):
     _fields_ = [("fusion", ctypes.c_int32), ("k_max", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("chunk_gates", ctypes.c_int32),
                 ("lookahead", ctypes.c_int32), ("compile_threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32)]
 
 
 class ProgramInfo(ctypes.Structure):
@@ -143,8 +143,8 @@ def _mats(m):
 
 
 def make_config(fusion=1, k_max=2, tile_bits=0, threads=0, chunk_gates=0, lookahead=0,
-                compile_threads=0) -> QsimConfig:
-    return QsimConfig(fusion, k_max, tile_bits, threads, chunk_gates, lookahead, compile_threads, 0)
+                compile_threads=0, persistent=0) -> QsimConfig:
+    return QsimConfig(fusion, k_max, tile_bits, threads, chunk_gates, lookahead, compile_threads, persistent)
 
 
 # ----------------------------------------------------------- torch plumbing --

@@ -269,3 +269,55 @@ def test_program_outlives_its_context():
     with pytest.raises(qs.QsimError):
         other.run(p)
     del p
+
+
+# --------------------------------------- rotation passes over subspace tiles --
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("n,tile_bits", [(16, 10), (16, 12), (21, 11), (21, 12), (21, 13), (21, 14)])
+def test_rotation_passes_uniform_angles(n, tile_bits, persistent):
+    """complex64 register-segment passes (one block per tile, or resident
+    blocks taking tiles from a counter) with angles over the whole circle, so
+    the Pauli frame splits about half of the rotations; mid-circuit
+    measurements flush it."""
+    c = W.ucc_circuit(n, seed=70 + n + tile_bits, n_gadgets=None, w_lo=2, w_hi=6, theta="uniform",
+                      target_gates=2500, n_meas=5)
+    ref, r = run_oracle(c, seed=13)
+    sim, st = run_gpu(c, "c64", seed=13, config=dict(fusion=2, tile_bits=tile_bits, persistent=persistent))
+    assert st == 0
+    out, prob = sim.outcomes()
+    check_outcomes("c64", out, prob, r, 13)
+    check_state("c64", sim.state(), ref)
+
+
+def test_persistent_passes_replay_and_recover_after_a_failed_assertion():
+    """A compiled program replayed several times keeps the tile counter in step;
+    a failed assertion makes later persistent passes leave the state alone
+    (while still consuming their tile numbers), and after a reset the same
+    program runs correctly again."""
+    n = 18
+    c = W.ucc_circuit(n, seed=5, n_gadgets=200, w_lo=2, w_hi=6, theta="uniform", target_gates=3000)
+    cfg = dict(fusion=2, tile_bits=12, persistent=1)
+    sim = qs.Sim(n, "c64", config=cfg)
+    prog = sim.compile(c.gates)
+    ref = oracle.basis_state(n)
+    for rep in range(3):
+        sim.run(prog)
+        assert sim.sync() == 0
+        oracle.run(ref, n, c.gates)
+        check_state("c64", sim.state(), ref)
+    # an assertion that fails: qubit 0 reset, flipped to |1>, then asserted to be |0>
+    bad = W.records([(OP["RESET"], 0, 0, 0, 0, 0), (OP["X"], 0, 0, 0, 0, 0),
+                     (OP["MEASURE"], 0, 0, 0, 0, 0, 1)])
+    sim.apply(bad)
+    assert sim.sync() == qs.E_ZEROPROB
+    frozen = sim.state()
+    sim.run(prog)                      # refused by every pass: the state stays
+    assert sim.sync() == qs.E_ZEROPROB
+    assert np.array_equal(sim.state(), frozen)
+    sim.reset()
+    sim.run(prog)
+    assert sim.sync() == 0
+    ref = oracle.basis_state(n)
+    oracle.run(ref, n, c.gates)
+    check_state("c64", sim.state(), ref)
+    prog.free()

@@ -196,6 +196,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def l2_copy_gbs(torch, n):
+    """Bandwidth of an L2-resident copy the size of the n-qubit complex64 state
+    (one read and one write of 2^n x 8 bytes), timed as a CUDA graph of 100
+    copies so that launch gaps do not dominate; best of 5."""
+    src = torch.ones((1 << n) * 2, dtype=torch.float32, device="cuda")
+    dst = torch.empty_like(src)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            dst.copy_(src)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(100):
+            dst.copy_(src)
+    best = None
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            g.replay()
+            e1.record(s)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 100 / 1e3
+        best = t if best is None else min(best, t)
+    return 2 * src.numel() * 4 / best / 1e9
+
+
 def run_ours(args):
     world, rank, local = dist_setup()
     import numpy as np
@@ -294,6 +323,7 @@ def run_ours(args):
     if rank != 0:
         return
     hbm_peak, src = peaks()
+    l2_gbs = l2_copy_gbs(torch, n)
     n_s = max(prof["samples"], 1)
     avg_ms = prof["ms"] / n_s
     flops_l = prof["flops"] / n_s
@@ -308,10 +338,22 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": mem_frac,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
-    roof.update({"traffic": None, "kernel": "k_tile_pass", "avg_launch_ms": avg_ms,
+    # DRAM traffic of one launch from the ncu capture summarised in
+    # profiles/rot_pass_21q_c64_m12.md (that exact configuration only)
+    traffic, traffic_src = None, None
+    if cfg.get("fusion") == 2 and cfg.get("tile_bits") == 12 and not cfg.get("threads") and not cfg.get("persistent"):
+        traffic = 16854528
+        traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, m = 12 "
+                       "(caches flushed before the launch: the state's cold read; writes stay in L2)")
+    roof.update({"traffic": traffic, "traffic_source": traffic_src,
+                 "kernel": "tile passes: k_rot_pass (register segments) and k_tile_pass",
+                 "avg_launch_ms": avg_ms,
                  "launch_samples": prof["samples"], "algorithmic_bytes_per_launch": bytes_l,
                  "algorithmic_flops_per_launch": flops_l, "memory_gbs": gbs,
-                 "memory_frac_of_hbm": mem_frac, "hbm_peak_gbs": hbm_peak})
+                 "memory_frac_of_hbm": mem_frac, "hbm_peak_gbs": hbm_peak,
+                 "l2_copy_gbs": l2_gbs, "frac_of_l2_copy": gbs / l2_gbs if l2_gbs else None,
+                 "l2_copy_source": "measured here: CUDA graph of 100 in-place copies of an L2-resident "
+                                   "buffer the size of the state (read + write bytes), best of 5"})
     launches = args.steps * (info["passes"] + 2 * info["measurements"] + 1 + 2)
     line = {
         "metric": "gates/s at 21 qubits (UCC-style circuit, complex64)",
@@ -428,8 +470,9 @@ def run_batched(args):
     def prog_flops(c):
         """(algorithmic flops of one run, bytes of the uploaded device program)."""
         ops = qs.fuse(c.n, c.gates, dtype=qs.C64, fusion=fusion, tile_bits=c.n if c.n <= 14 else 0)
-        dense = [o for o in ops if o[0] not in ("event", "pauli")]
-        fpa = 8 * (len(ops) - len(dense)) + sum(8 << o[0] for o in dense)
+        dense = [o for o in ops if isinstance(o[0], int)]
+        n_rot = sum(1 for o in ops if o[0] in ("pauli", "frame"))
+        fpa = 8 * n_rot + sum(8 << o[0] for o in dense)
         nbytes = 16 * len(ops) + 8 * (len(ops) - len(dense) + sum(4 ** o[0] for o in dense))
         return fpa * (1 << c.n), nbytes
     f_set, b_set = prog_flops(cs[0])
@@ -600,8 +643,9 @@ def run_serving(args):
         if pi not in fl_cache:
             c = pool[pi]
             ops = qs.fuse(c.n, c.gates, dtype=qs.C64, fusion=fusion, tile_bits=c.n if c.n <= 14 else 0)
-            dense = [o for o in ops if o[0] not in ("event", "pauli")]
-            fl_cache[pi] = (8 * (len(ops) - len(dense)) + sum(8 << o[0] for o in dense)) * (1 << c.n)
+            dense = [o for o in ops if isinstance(o[0], int)]
+            n_rot = sum(1 for o in ops if o[0] in ("pauli", "frame"))
+            fl_cache[pi] = (8 * n_rot + sum(8 << o[0] for o in dense)) * (1 << c.n)
         return fl_cache[pi]
     flops = sum(req_flops(meta[i][0]) for i in results)
     tflops = flops / window / 1e12

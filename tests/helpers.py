@@ -8,6 +8,8 @@ import math
 
 import numpy as np
 
+from paper_2310_17739_gb300 import workload as W
+
 I2 = np.eye(2, dtype=np.complex128)
 PX = np.array([[0, 1], [1, 0]], dtype=np.complex128)
 PY = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
@@ -105,3 +107,31 @@ def load_mma_table(path):
             parts = line.split()
             rows[parts[0]] = [float(v) for v in parts[1:]]
     return rows
+
+
+SELF_INVERSE = {"ID", "X", "Y", "Z", "H", "CX", "CY", "CZ", "SWAP", "BARRIER"}
+NEGATE_ANGLE = {"RX", "RY", "RZ", "U1", "CRX", "CRY", "CRZ", "CU1", "RXX", "RZZ"}
+
+
+def invert_records(g):
+    """Gate records of the inverse circuit (reversed order, each gate inverted),
+    for the gates whose inverse is the gate itself or its negated angle."""
+    inv = g[::-1].copy()
+    names = {v: k for k, v in W.OP.items()}
+    orig = inv["op"].copy()          # rules select on the original op codes
+    for op in np.unique(orig):
+        name = names[int(op)]
+        sel = orig == op
+        if name in NEGATE_ANGLE:
+            inv["p"][sel, 0] = -inv["p"][sel, 0]
+        elif name == "S":
+            inv["op"][sel] = W.OP["SDG"]
+        elif name == "SDG":
+            inv["op"][sel] = W.OP["S"]
+        elif name == "T":
+            inv["op"][sel] = W.OP["TDG"]
+        elif name == "TDG":
+            inv["op"][sel] = W.OP["T"]
+        elif name not in SELF_INVERSE:
+            raise ValueError(f"no inverse rule for {name}")
+    return inv

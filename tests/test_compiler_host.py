@@ -426,3 +426,18 @@ def test_pauli_schedule_reordering_is_exact(tile_bits):
         else:
             seg.append(o)
     assert np.abs(psi - ref).max() < 1e-11
+
+
+def test_inverse_records_undo_the_circuit():
+    """The test helper that builds inverse circuits (used by the full-size GPU
+    round trip) is itself checked against the oracle."""
+    n = 7
+    c = W.ucc_circuit(n, seed=12, n_gadgets=30, w_lo=2, w_hi=6, theta="uniform", target_gates=900)
+    extra = W.random_circuit(n, 200, seed=3, ops=[OP[k] for k in ("H", "S", "T", "SDG", "TDG", "RX", "RY",
+                                                                   "RZ", "CX", "CZ", "SWAP", "RZZ")]).gates
+    g = np.concatenate([c.gates, extra])
+    psi = W.random_state(n, seed=4)
+    ref = psi.copy()
+    oracle.run(ref, n, g)
+    oracle.run(ref, n, H.invert_records(g))
+    assert np.abs(ref - psi).max() < 1e-12

@@ -695,6 +695,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
     const int L = forced_low_bits(dtype, m);
     const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
     const size_t W = cfg.lookahead > 0 ? (size_t)cfg.lookahead : 64;
+    const bool reg_candidate = dtype == QSIM_C64 && !out.resident && m >= 10 && m <= 14;
     const int k_max = std::max(2, std::min(cfg.k_max > 0 ? cfg.k_max : 2, std::min(5, m)));
 
     // Doubly linked list over not-yet-scheduled ops (in stream order).
@@ -852,6 +853,12 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
                 break;
             const uint64_t Q = o.mask();
             bool ok = (out.resident || fits(V, o, m)) && !(Q & blocked_np);
+            // a complex64 rotation-only pass runs as register segments, which
+            // hold a rotation whose tile coordinates span at most 5 bits: a
+            // wider one (an X mask already in the span) waits for a later pass
+            if (ok && reg_candidate && only_rot && o.pauli() && V.contains(o.xm) &&
+                popc(V.coords(o.xm)) > 5)
+                ok = false;
             if (ok && (Q & blocked_p)) {
                 if (!o.pauli()) ok = false;
                 else

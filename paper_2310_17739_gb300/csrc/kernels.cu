@@ -575,8 +575,8 @@ __device__ __forceinline__ void seg_load_smem(float2 *reg, uint32_t addr, const 
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_rot_pass(TileArgs a) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     float2 *mats_s = tile + (1u << a.m);
@@ -1122,8 +1122,9 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 512, 2>));
     QSIM_ATTR((k_tile_pass<float, 256, 5>));
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
-    QSIM_ATTR(k_rot_pass<256>);
-    QSIM_ATTR(k_rot_pass<512>);
+    QSIM_ATTR((k_rot_pass<128, 4>));
+    QSIM_ATTR((k_rot_pass<256, 2>));
+    QSIM_ATTR((k_rot_pass<512, 1>));
     QSIM_ATTR(k_rot_pipe<64>);
     QSIM_ATTR(k_rot_pipe<128>);
     QSIM_ATTR(k_rot_pipe<256>);
@@ -1233,8 +1234,10 @@ cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const ui
     if (!make_tile_args(0, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
         return cudaErrorInvalidValue;
     a.scale = scale;
-    if (m <= 13) return launch_dependent(k_rot_pass<256>, 1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s, a);
-    return launch_dependent(k_rot_pass<512>, 1u << (n - m), 1u << (m - 5), tile_smem_bytes(0, m), s, a);
+    const unsigned grid = 1u << (n - m), threads = 1u << (m - 5);
+    if (m == 12) return launch_dependent(k_rot_pass<128, 4>, grid, threads, tile_smem_bytes(0, m), s, a);
+    if (m <= 13) return launch_dependent(k_rot_pass<256, 2>, grid, threads, tile_smem_bytes(0, m), s, a);
+    return launch_dependent(k_rot_pass<512, 1>, grid, threads, tile_smem_bytes(0, m), s, a);
 }
 
 cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,

@@ -177,6 +177,14 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
         };
         emit_body();
         bool reg = allow_reg && reg_dtype && all_rot && src.gadget && hp.n <= 32;
+        // the generic tile kernel wants the basis vectors after the leading
+        // unit ones free of those low bits (whole 16-byte runs per row)
+        auto reduce_basis = [&]() {
+            int l = 0;
+            while (l < m && B[l] == (1ull << l)) l++;
+            const uint64_t low = l >= 64 ? ~0ull : ((1ull << l) - 1);
+            for (int j = l; j < m; j++) B[j] &= ~low;
+        };
         if (reg) {
             // scaled form: every cosine is >= 1/sqrt(2) after the Pauli frame
             double scale = 1.0;
@@ -197,12 +205,7 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             }
         }
         if (!reg && src.gadget) {
-            // the generic tile kernel wants the basis vectors after the leading
-            // unit ones free of those low bits (whole 16-byte runs per row)
-            int l = 0;
-            while (l < m && B[l] == (1ull << l)) l++;
-            const uint64_t low = l >= 64 ? ~0ull : ((1ull << l) - 1);
-            for (int j = l; j < m; j++) B[j] &= ~low;
+            reduce_basis();
             emit_body();
         }
         fused += body.size();
@@ -317,7 +320,8 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                 continue;
             }
             // too many ops for one register-segment pass: the generic kernel
-            // runs it, with plain (cos, W) coefficients
+            // runs it, with plain (cos, W) coefficients over the reduced basis
+            reduce_basis();
             emit_body();
             p.scale = 1.0f;
         }
@@ -1421,7 +1425,8 @@ qsim_status build_tiled_plan(qsim_batch *b, bool may_upload) {
                     qsim::TileArgs a;
                     if (!qsim::make_tile_args(b->dtype, ic->state, ic->n, dc.m, p.tile, dc.bvec.data() + p.basis,
                                               dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
-                                              p.mat_count, ic->ctl, &a))
+                                              p.mat_count, ic->ctl, &a) ||
+                        !qsim::generic_tile_ok(a))
                         return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernel");
                     a.pad = (uint32_t)std::max(dc.kmax, 1);  // op size, read back below
                     b->tiled_descs.push_back(a);

@@ -1205,12 +1205,15 @@ cudaError_t launch_dependent(Kern kern, unsigned grid, unsigned block, size_t sm
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+bool generic_tile_ok(const TileArgs &a) { return (1 << (a.m - a.L)) <= kMaxHi; }
+
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
                              uint64_t pivots, const uint64_t *basis, const DevOp *ops, uint32_t n_ops,
                              const void *mats, uint32_t mat_first, uint32_t mat_count,
                              const MeasCtl *ctl, cudaStream_t s) {
     TileArgs a;
-    if (!make_tile_args(dtype, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
+    if (!make_tile_args(dtype, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a) ||
+        !generic_tile_ok(a))
         return cudaErrorInvalidValue;
     const unsigned grid = 1u << (n - m);
     const size_t smem = tile_smem_bytes(dtype, m);

@@ -116,6 +116,10 @@ struct TileArgs {
 bool make_tile_args(int dtype, void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
                     const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
                     uint32_t mat_count, const MeasCtl *ctl, TileArgs *out);
+// Whether the generic tile pass (k_tile_pass, k_tile_pass_multi) can run a
+// tile: it tabulates the offsets of the 2^(m-L) tile rows in a fixed shared
+// array of 1024 entries.
+bool generic_tile_ok(const TileArgs &a);
 // A complex64 pass of rotations laid out in register segments (see
 // kSegMarker): 2^(m-5) threads, 32 amplitudes each; 10 <= m <= 14, n <= 32.
 // Its rotations carry (cos, t = W / cos) and run as a' = a + t (...) with the

@@ -321,3 +321,20 @@ def test_persistent_passes_replay_and_recover_after_a_failed_assertion():
     oracle.run(ref, n, c.gates)
     check_state("c64", sim.state(), ref)
     prog.free()
+
+
+def test_long_run_of_one_rotation_falls_back_to_the_generic_pass():
+    """300 repeats of one Pauli rotation whose X mask touches qubit 0 fill a
+    register-segment pass beyond its op limit; that pass runs in the generic
+    kernel over the row-reduced basis and still matches the oracle."""
+    n = 16
+    rows = []
+    for r in range(300):
+        rows += W.gadget_rows([0, 5, 9], "XZY", 0.01 * (r % 17) - 0.08)
+    g = W.records([(op, q0, q1, p, 0, 0) for op, q0, q1, p in rows])
+    c = W.Circuit(n, np.concatenate([W.ucc_circuit(n, seed=8, n_gadgets=20, w_lo=2, w_hi=5,
+                                                   target_gates=400).gates, g]))
+    ref, _ = run_oracle(c)
+    sim, st = run_gpu(c, "c64", config=dict(fusion=2, tile_bits=12))
+    assert st == 0
+    check_state("c64", sim.state(), ref)

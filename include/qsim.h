@@ -242,15 +242,17 @@ QSIM_API qsim_status qsim_reset_state(qsim_ctx *ctx);
 /* Device pointer of the state (valid until qsim_destroy) and its size. */
 QSIM_API qsim_status qsim_state_ptr(qsim_ctx *ctx, void **dptr, size_t *bytes);
 /* ---------------------------------------------------------------- timing --
- * Sampled device timing of the tile-pass kernel (the gate-application sweep of
- * Eq. (1q-op)/(2q-op) over shared-memory tiles).  After qsim_profile_start
- * with every > 0, every every-th tile-pass launch is bracketed by CUDA events
- * recorded on the context stream (at most 8192 samples; every = 0 stops).
+ * Sampled device timing of the tile passes (the gate-application sweep of
+ * Eq. (1q-op)/(2q-op) over tiles).  After qsim_profile_start with every > 0, a
+ * window of min(every, 16) consecutive tile-pass launches starting at every
+ * every-th launch is bracketed by CUDA events recorded on the context stream
+ * (dependent launches inside a window keep overlapping; a window closes early
+ * at a measurement; at most 8192 windows; every = 0 stops).
  * qsim_profile_read synchronises and returns, for the sampled launches, the
- * summed device time (ms), their count, their algorithmic flops (8 * 2^k real
- * flops per amplitude per dense k-qubit op) and algorithmic bytes (one read
- * and one write of the state per launch), and the number of tile-pass launches
- * since the start. */
+ * summed device time of the windows (ms), the number of launches in them,
+ * their algorithmic flops (8 * 2^k real flops per amplitude per dense k-qubit
+ * op, 8 per rotation) and algorithmic bytes (one read and one write of the
+ * state per launch), and the number of tile-pass launches since the start. */
 QSIM_API qsim_status qsim_profile_start(qsim_ctx *ctx, int every);
 QSIM_API qsim_status qsim_profile_read(qsim_ctx *ctx, double *sampled_ms, uint64_t *n_sampled,
                                        double *sampled_flops, double *sampled_bytes,

@@ -373,7 +373,10 @@ struct qsim_ctx {
     // sampled tile-pass timing
     int prof_every = 0;
     uint64_t prof_launches = 0;
-    size_t prof_used = 0;
+    size_t prof_used = 0;       // closed windows (event pairs)
+    bool prof_open = false;     // a window's start event is recorded
+    uint32_t prof_in_window = 0;
+    uint64_t prof_sampled = 0;  // tile-pass launches inside closed windows
     double prof_flops = 0, prof_bytes = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     // live programs compiled on this context (released and orphaned by qsim_destroy)
@@ -567,6 +570,19 @@ qsim_status launch_measure(qsim_ctx *c, int q, int mode, int reset, uint64_t see
     return QSIM_OK;
 }
 
+// Launch timing windows: up to kProfWindow consecutive tile-pass launches
+// between two events, so that dependent launches inside a window still overlap.
+constexpr int kProfWindow = 16;
+
+cudaError_t profile_close(qsim_ctx *c) {
+    if (!c->prof_open) return cudaSuccess;
+    c->prof_open = false;
+    const cudaError_t e = cudaEventRecord(c->prof_ev[c->prof_used].second, c->stream);
+    c->prof_used++;
+    c->prof_sampled += c->prof_in_window;
+    return e;
+}
+
 qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
     // 512 threads per tile for complex64 rotation passes (more warps in flight);
     // dense C2 passes and complex128 keep 256 (their 512-thread builds are capped
@@ -597,14 +613,18 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
     }
     for (const Pass &p : dc.passes) {
         if (p.ev) {
+            CK(profile_close(c), "profile event");  // a window never spans a measurement
             qsim_status s = launch_measure(c, (int)p.q, p.flags, p.ev == qsim::EV_RESET, c->seed);
             if (s != QSIM_OK) return s;
             continue;
         }
         if (!p.count) continue;
-        const bool sample = c->prof_every > 0 && c->prof_launches % (uint64_t)c->prof_every == 0 &&
-                            c->prof_used < c->prof_ev.size();
-        if (sample) CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
+        if (!c->prof_open && c->prof_every > 0 && c->prof_launches % (uint64_t)c->prof_every == 0 &&
+            c->prof_used < c->prof_ev.size()) {
+            CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
+            c->prof_open = true;
+            c->prof_in_window = 0;
+        }
         const uint64_t *basis = dc.bvec.data() + p.basis;
         if (p.reg && c->cfg.persistent && dc.m <= 13) {
             if (!c->tile_ctr) {
@@ -629,11 +649,12 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
                                       dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
                                       p.mat_count, c->ctl, c->stream),
                "tile pass launch");
-        if (sample) {
-            CK(cudaEventRecord(c->prof_ev[c->prof_used].second, c->stream), "profile event");
-            c->prof_used++;
+        if (c->prof_open) {
+            c->prof_in_window++;
             c->prof_flops += (double)p.fpa * (double)(1ull << c->n);
             c->prof_bytes += 2.0 * (double)c->state_bytes;
+            if (c->prof_in_window >= (uint32_t)std::min(c->prof_every, kProfWindow))
+                CK(profile_close(c), "profile event");
         }
         c->prof_launches++;
     }
@@ -1116,6 +1137,9 @@ qsim_status qsim_profile_start(qsim_ctx *c, int every) {
     c->prof_every = every;
     c->prof_launches = 0;
     c->prof_used = 0;
+    c->prof_open = false;
+    c->prof_in_window = 0;
+    c->prof_sampled = 0;
     c->prof_flops = c->prof_bytes = 0;
     return QSIM_OK;
 }
@@ -1124,6 +1148,7 @@ qsim_status qsim_profile_read(qsim_ctx *c, double *ms, uint64_t *n_sampled, doub
                               uint64_t *n_launches) {
     qsim_status s = check_usable(c);
     if (s != QSIM_OK) return s;
+    CK(profile_close(c), "profile event");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     double tot = 0;
     for (size_t i = 0; i < c->prof_used; i++) {
@@ -1132,7 +1157,7 @@ qsim_status qsim_profile_read(qsim_ctx *c, double *ms, uint64_t *n_sampled, doub
         tot += t;
     }
     if (ms) *ms = tot;
-    if (n_sampled) *n_sampled = c->prof_used;
+    if (n_sampled) *n_sampled = c->prof_sampled;
     if (flops) *flops = c->prof_flops;
     if (bytes) *bytes = c->prof_bytes;
     if (n_launches) *n_launches = c->prof_launches;

@@ -338,3 +338,25 @@ def test_long_run_of_one_rotation_falls_back_to_the_generic_pass():
     sim, st = run_gpu(c, "c64", config=dict(fusion=2, tile_bits=12))
     assert st == 0
     check_state("c64", sim.state(), ref)
+
+
+def test_profile_windows_count_launches_and_bytes():
+    """Launch timing windows: every tile-pass launch inside a window is counted
+    once with one read and one write of the state; windows close at
+    measurements; the sampled time per launch is positive and the whole run's
+    launches are counted."""
+    n = 18
+    c = W.ucc_circuit(n, seed=31, n_gadgets=None, w_lo=2, w_hi=6, theta="uniform", target_gates=6000, n_meas=3)
+    sim = qs.Sim(n, "c64", config=dict(fusion=2, tile_bits=12))
+    sim.profile_start(4)
+    sim.apply(c.gates)
+    assert sim.sync() == 0
+    prof = sim.profile_read()
+    prog = sim.compile(c.gates)
+    passes = prog.info()["passes"]          # tile passes (measurements are not counted)
+    prog.free()
+    assert prof["launches"] == passes
+    assert 0 < prof["samples"] <= prof["launches"]
+    assert prof["bytes"] == prof["samples"] * 2 * 8 * (1 << n)
+    assert prof["ms"] > 0
+    sim.profile_start(0)

@@ -12,7 +12,8 @@ Pins (all in ``tests/test_oracle_*.py``): dense Kronecker products of every
 gate on <= 6 qubits, scipy ``expm`` for every rotation, GHZ and QFT closed
 forms, exp(-i t P) = cos t I - i sin t P for compiled Pauli gadgets, norm and
 U-then-U^dagger invariants, Born statistics, the probability-product of the
-mid-circuit measurement assertion table, and numpy's Philox for the draws.
+mid-circuit measurement assertion table, numpy's Philox for the draws, and
+numpy's searchsorted on the cumulative Born distribution for final-state shots.
 """
 from __future__ import annotations
 
@@ -66,6 +67,10 @@ def lib():
             L.oracle_philox4x64_10.argtypes = [dp, dp, dp]
             L.oracle_draw.argtypes = [u64, u64]
             L.oracle_draw.restype = ctypes.c_double
+            L.oracle_shot_draw.argtypes = [u64, u64]
+            L.oracle_shot_draw.restype = ctypes.c_double
+            L.oracle_sample.argtypes = [dp, ctypes.c_int, u64, u64, u64, dp]
+            L.oracle_sample.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -152,3 +157,18 @@ def philox_block(ctr, key) -> np.ndarray:
 
 def draw(seed: int, k: int) -> float:
     return float(lib().oracle_draw(seed, k))
+
+
+def shot_draw(seed: int, s: int) -> float:
+    """The uniform draw of final-state shot s (Philox counter (s, 1, 0, 0))."""
+    return float(lib().oracle_shot_draw(seed, s))
+
+
+def sample(psi: np.ndarray, n: int, shots: int, seed: int, mask: int | None = None) -> np.ndarray:
+    """Final-state shots from |psi|^2: packed bits of `mask` (default: all qubits)."""
+    mask = (1 << n) - 1 if mask is None else mask
+    out = np.zeros(max(shots, 1), dtype=np.uint64)
+    st = lib().oracle_sample(_ptr(psi), n, mask, shots, seed, _ptr(out))
+    if st:
+        raise MemoryError("oracle_sample: no memory for the cumulative distribution")
+    return out[:shots]

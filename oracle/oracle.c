@@ -38,6 +38,13 @@
  *                    random numbers: as easy as 1, 2, 3" (SC'11).  The draw
  *                    u(seed,k) = (word 0 of the block with counter (k,0,0,0)
  *                    and key (seed,0)) >> 11, times 2^-53.
+ *   oracle_sample    final-state sampling (the register read-out `measure q
+ *                    -> c` of Listing "Block structure ...", taken m times
+ *                    from one state without collapse): shot s draws
+ *                    v(seed,s) from the block with counter (s,1,0,0) and
+ *                    returns the smallest index x with v * total <
+ *                    sum_{i<=x} |a_i|^2 (Born rule, cumulative sum in index
+ *                    order), the bits of a mask packed in ascending order.
  */
 #include <complex.h>
 #include <math.h>
@@ -275,6 +282,52 @@ double oracle_draw(uint64_t seed, uint64_t k)
     uint64_t ctr[4] = { k, 0, 0, 0 }, key[2] = { seed, 0 }, out[4];
     oracle_philox4x64_10(ctr, key, out);
     return (double)(out[0] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+double oracle_shot_draw(uint64_t seed, uint64_t s)
+{
+    uint64_t ctr[4] = { s, 1, 0, 0 }, key[2] = { seed, 0 }, out[4];
+    oracle_philox4x64_10(ctr, key, out);
+    return (double)(out[0] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ----------------------------------------------------------- sampling -- */
+
+static uint64_t og_pack_bits(uint64_t x, uint64_t mask)
+{
+    uint64_t r = 0;
+    int j = 0;
+    for (int b = 0; b < 64; b++)
+        if ((mask >> b) & 1) {
+            r |= ((x >> b) & 1) << j;
+            j++;
+        }
+    return r;
+}
+
+/* Returns 0, or 1 when the cumulative array cannot be allocated. */
+int oracle_sample(const double *psi, int n, uint64_t mask, uint64_t shots, uint64_t seed, uint64_t *out)
+{
+    const cd *a = (const cd *)psi;
+    const uint64_t N = (uint64_t)1 << n;
+    double *cum = (double *)malloc(N * sizeof(double));
+    if (!cum) return 1;
+    double acc = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        acc += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+        cum[i] = acc;
+    }
+    for (uint64_t s = 0; s < shots; s++) {
+        const double target = oracle_shot_draw(seed, s) * acc;
+        uint64_t lo = 0, hi = N - 1;   /* smallest x with cum[x] > target */
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo) / 2;
+            if (cum[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        out[s] = og_pack_bits(lo, mask);
+    }
+    free(cum);
+    return 0;
 }
 
 /* -------------------------------------------------------- measurement -- */

@@ -393,3 +393,50 @@ def test_z_expectation_is_p0_minus_p1():
     for q in range(n):
         p0, p1 = oracle.prob(psi, n, q)
         assert abs(z[q] - (p0 - p1)) < 1e-13
+
+
+# ------------------------------------------------------- final-state shots ----
+@pytest.mark.parametrize("seed,s", [(0, 0), (7, 1), (1003, 999), (2**63 + 1, 2**33)])
+def test_shot_draw_matches_numpy(seed, s):
+    """Shot s draws from the Philox block at counter (s, 1, 0, 0)."""
+    c_int = s + (1 << 64)
+    bg = np.random.Philox(key=np.array([seed, 0], dtype=np.uint64), counter=c_int - 1)
+    ref = bg.random_raw(4)
+    assert oracle.shot_draw(seed, s) == (int(ref[0]) >> 11) * 2.0**-53
+
+
+def test_sample_is_the_inverse_cumulative_distribution():
+    """Every shot is numpy.searchsorted of its draw on the cumulative Born
+    distribution (the smallest index whose cumulative probability exceeds
+    draw * total), with the masked bits packed in ascending order."""
+    n = 9
+    psi = W.random_state(n, seed=21)
+    psi[::3] = 0                      # zero-probability indices must never be drawn
+    cum = np.cumsum(np.abs(psi) ** 2)
+    shots = oracle.sample(psi, n, 3000, seed=17)
+    u = np.array([oracle.shot_draw(17, s) for s in range(3000)])
+    x = np.searchsorted(cum, u * cum[-1], side="right")
+    assert np.array_equal(shots, x)
+    assert not np.any(shots % 3 == 0)
+    mask = 0b101010010
+    packed = oracle.sample(psi, n, 3000, seed=17, mask=mask)
+    bits = [b for b in range(n) if (mask >> b) & 1]
+    ref = sum(((x >> b) & 1) << j for j, b in enumerate(bits))
+    assert np.array_equal(packed, ref)
+
+
+def test_sample_born_statistics_and_special_states():
+    n = 4
+    psi = W.random_state(n, seed=5)
+    p = np.abs(psi) ** 2
+    shots = oracle.sample(psi, n, 40000, seed=3)
+    counts = np.bincount(shots.astype(np.int64), minlength=1 << n)
+    chi2, pval = scipy.stats.chisquare(counts, p * 40000)
+    assert pval > 1e-4
+    # a basis state always gives its own index; a uniform superposition is uniform
+    e = np.zeros(1 << n, dtype=np.complex128)
+    e[11] = 1
+    assert np.all(oracle.sample(e, n, 100, seed=1) == 11)
+    u = np.full(1 << n, 0.25, dtype=np.complex128)
+    counts = np.bincount(oracle.sample(u, n, 32000, seed=2).astype(np.int64), minlength=16)
+    assert scipy.stats.chisquare(counts).pvalue > 1e-4

@@ -294,6 +294,11 @@ def run_ours(args):
         ms = float(t.item())
     out, probs = sim.outcomes()
     value = c.G * args.steps * world / (ms / 1e3)
+    # side measurement: final-state shots of the end state (qsim_sample)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    shots = sim.sample(1_000_000, seed=5)
+    t_shots = time.perf_counter() - t0
 
     # end to end through the public API from host gate records
     e2e = None
@@ -356,6 +361,9 @@ def run_ours(args):
                  "l2_copy_source": "measured here: CUDA graph of 100 in-place copies of an L2-resident "
                                    "buffer the size of the state (read + write bytes), best of 5"})
     launches = args.steps * (info["passes"] + 2 * info["measurements"] + 1 + 2)
+    sampling = {"shots": int(shots.size), "seconds": t_shots, "shots_per_s": shots.size / t_shots,
+                "includes": "FP64 prefix sums of the 2^21 Born weights, 1e6 Philox draws and searches, "
+                            "read-back to host (qsim_sample)"}
     line = {
         "metric": "gates/s at 21 qubits (UCC-style circuit, complex64)",
         "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
@@ -381,6 +389,7 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
         "outcomes": "".join(str(int(x)) for x in out[:64]),
+        "final_state_sampling": sampling,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.cpu_seconds)

@@ -236,6 +236,20 @@ QSIM_API qsim_status qsim_expect(qsim_ctx *ctx, const qsim_pauli_term *terms, si
  * qsim_state synchronises.  qsim_reset_state restores |0...0> and clears the
  * draw ordinal, the outcome log, the success product and a failed-assertion
  * mark. */
+/* Final-state shots (the register read-out `measure q -> c` of Listing "Block
+ * structure ...", taken `shots` times from the current state without collapse;
+ * the counterpart of the measurement assertion's repeated runs, Section
+ * "Mid-Circuit Measurement Assertion").  Shot s draws v = (word 0 of the
+ * Philox4x64-10 block with counter (s, 1, 0, 0) and key (seed, 0)) >> 11 times
+ * 2^-53 and takes the smallest index x with v * total < sum_{i <= x} |a_i|^2
+ * (total = sum of all |a_i|^2; FP64 sums of FP64 squares); out[s] (host memory,
+ * `shots` entries) receives the bits of x selected by qubit_mask packed in
+ * ascending order.  The state is not changed and the measurement ordinal does
+ * not advance.  QSIM_E_INVAL: mask beyond n qubits, out NULL with shots > 0,
+ * or shots > 2^40; QSIM_E_OOM: no device memory for the 2^n / 512 partial sums
+ * and the shots; synchronises. */
+QSIM_API qsim_status qsim_sample(qsim_ctx *ctx, uint64_t qubit_mask, uint64_t shots, uint64_t seed,
+                                 uint64_t *out);
 QSIM_API qsim_status qsim_state(qsim_ctx *ctx, void *dst, size_t bytes, int dst_is_device);
 QSIM_API qsim_status qsim_set_state(qsim_ctx *ctx, const void *src, size_t bytes, int src_is_device);
 QSIM_API qsim_status qsim_reset_state(qsim_ctx *ctx);

@@ -1070,6 +1070,39 @@ qsim_status qsim_expect(qsim_ctx *c, const qsim_pauli_term *t, size_t nt, double
     return sync_read(c);
 }
 
+qsim_status qsim_sample(qsim_ctx *c, uint64_t qubit_mask, uint64_t shots, uint64_t seed, uint64_t *out) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    const uint64_t full = c->n >= 64 ? ~0ull : ((1ull << c->n) - 1ull);
+    if (qubit_mask & ~full) return fail(c, QSIM_E_INVAL, "qubit mask beyond n qubits");
+    if (shots && !out) return fail(c, QSIM_E_INVAL, "null out");
+    if (shots > (1ull << 40)) return fail(c, QSIM_E_INVAL, "too many shots");
+    const uint64_t P = (1ull << c->n) / (uint64_t)qsim::sample_chunk(c->n);
+    const size_t pb = (size_t)P * sizeof(double), ob = (size_t)(P + 1) * sizeof(double);
+    const size_t sb = (size_t)std::max<uint64_t>(shots, 1) * sizeof(uint64_t);
+    double *d_part = (double *)dalloc(c, pb);
+    double *d_off = (double *)dalloc(c, ob);
+    uint64_t *d_out = (uint64_t *)dalloc(c, sb);
+    if (!d_part || !d_off || !d_out) {
+        dfree(c, d_part, pb);
+        dfree(c, d_off, ob);
+        dfree(c, d_out, sb);
+        return fail(c, QSIM_E_OOM, "sampling buffers");
+    }
+    cudaError_t e = qsim::launch_sample(c->dtype, c->state, c->n, qubit_mask, shots, seed, d_part, d_off, d_out,
+                                        c->stream);
+    if (e != cudaSuccess) s = cuda_fail(c, e, "sample launch");
+    if (s == QSIM_OK && shots) {
+        e = cudaMemcpyAsync(out, d_out, (size_t)shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "sample readback");
+    }
+    dfree(c, d_part, pb);
+    dfree(c, d_off, ob);
+    dfree(c, d_out, sb);
+    if (s != QSIM_OK) return s;
+    return sync_read(c);
+}
+
 qsim_status qsim_state(qsim_ctx *c, void *dst, size_t bytes, int dst_is_device) {
     qsim_status s = check_usable(c);
     if (s != QSIM_OK) return s;

@@ -71,10 +71,10 @@ __device__ __forceinline__ uint64_t ins0_64(uint64_t x, int p) {
 // ------------------------------------------------------ Philox4x64-10 --
 // Salmon et al., SC'11: 10 rounds of the 4x64 bijection with key schedule
 // k += (W0, W1) between rounds.
-__device__ __forceinline__ uint64_t philox_word0(uint64_t ctr0, uint64_t seed) {
+__device__ __forceinline__ uint64_t philox_word0(uint64_t ctr0, uint64_t seed, uint64_t ctr1 = 0) {
     const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
     const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-    uint64_t c0 = ctr0, c1 = 0, c2 = 0, c3 = 0, k0 = seed, k1 = 0;
+    uint64_t c0 = ctr0, c1 = ctr1, c2 = 0, c3 = 0, k0 = seed, k1 = 0;
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         if (r) {
@@ -655,6 +655,109 @@ __global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
 #pragma unroll
         for (int j = 0; j < 5; j++) sd_prev[j] = sd[j];
         i += 1 + nseg;
+    }
+}
+
+// --------------------------------------------------- final-state shots --
+// Shots of the Born distribution without collapse: FP64 partial sums of
+// |a_i|^2 over chunks of consecutive indices, their exclusive prefix sums,
+// then one warp per shot: shot s draws v from the Philox block at counter
+// (s, 1, 0, 0), finds the chunk whose prefix interval holds v * total (binary
+// search) and the first index of the chunk whose running sum exceeds it (warp
+// scan), and writes the bits of the mask packed in ascending order.
+template <typename R>
+__global__ void __launch_bounds__(256) k_sample_partials(const void *state, uint32_t chunk, double *partials) {
+    using T = typename V2<R>::T;
+    const T *a = reinterpret_cast<const T *>(state) + (uint64_t)blockIdx.x * chunk;
+    double acc = 0;
+    for (uint32_t i = threadIdx.x; i < chunk; i += 256) acc += norm2(a[i]);
+    __shared__ double red[256 / 32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < 256 / 32; w++) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// One block of 1024 threads: offsets[b] = sum of partials[0..b), offsets[P] = total.
+__global__ void __launch_bounds__(1024) k_sample_scan(const double *partials, uint32_t P, double *offsets) {
+    __shared__ double seg[1024];
+    const uint32_t per = (P + 1023) / 1024;
+    const uint32_t lo = min(P, threadIdx.x * per), hi = min(P, lo + per);
+    double t = 0;
+    for (uint32_t i = lo; i < hi; i++) t += partials[i];
+    seg[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive prefix of the 1024 segment sums
+        double run = 0;
+        for (int i = 0; i < 1024; i++) {
+            const double v = seg[i];
+            seg[i] = run;
+            run += v;
+        }
+        offsets[P] = run;
+    }
+    __syncthreads();
+    double run = seg[threadIdx.x];
+    for (uint32_t i = lo; i < hi; i++) {
+        offsets[i] = run;
+        run += partials[i];
+    }
+}
+
+__device__ __forceinline__ uint64_t pack_bits(uint64_t x, uint64_t mask) {
+    uint64_t r = 0;
+    int j = 0;
+    for (int b = 0; b < 64; b++)
+        if ((mask >> b) & 1ull) r |= ((x >> b) & 1ull) << j++;
+    return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_sample_draw(const void *state, uint32_t chunk, uint32_t P,
+                                                     const double *offsets, uint64_t seed, uint64_t shots,
+                                                     uint64_t mask, uint64_t *out) {
+    using T = typename V2<R>::T;
+    const T *a = reinterpret_cast<const T *>(state);
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const double total = offsets[P];
+    for (uint64_t s = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < shots; s += warps) {
+        const double v = (double)(philox_word0(s, seed, 1) >> 11) * (1.0 / 9007199254740992.0);
+        const double target = v * total;
+        // last chunk whose prefix is <= target
+        uint32_t lo = 0, hi = P - 1;
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (offsets[mid] <= target) lo = mid;
+            else hi = mid - 1;
+        }
+        uint64_t x = ~0ull, last_nz = ~0ull;
+        for (uint32_t b = lo; b < P && x == ~0ull; b++) {
+            double base = offsets[b];
+            const uint64_t first = (uint64_t)b * chunk;
+            for (uint32_t j = 0; j < chunk && x == ~0ull; j += 32) {
+                const uint32_t i = j + lane;
+                const double w = i < chunk ? norm2(a[first + i]) : 0.0;
+                double inc = w;  // inclusive warp scan in lane order
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= (unsigned)o) inc += t;
+                }
+                const unsigned hit = __ballot_sync(0xffffffffu, i < chunk && w > 0 && base + inc > target);
+                const unsigned nz = __ballot_sync(0xffffffffu, i < chunk && w > 0);
+                if (hit) x = first + j + (__ffs(hit) - 1);
+                else if (nz) last_nz = first + j + (31 - __clz(nz));
+                base += __shfl_sync(0xffffffffu, inc, 31);
+            }
+        }
+        if (x == ~0ull) x = last_nz;  // rounding put the target past the last nonzero entry
+        if (lane == 0) out[s] = pack_bits(x == ~0ull ? 0 : x, mask);
     }
 }
 
@@ -1277,6 +1380,25 @@ cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const ui
     if (m <= 11) return cudaLaunchKernelEx(&cfg, k_rot_pipe<64>, a, ctr, base, n_tiles);
     if (m == 12) return cudaLaunchKernelEx(&cfg, k_rot_pipe<128>, a, ctr, base, n_tiles);
     return cudaLaunchKernelEx(&cfg, k_rot_pipe<256>, a, ctr, base, n_tiles);
+}
+
+int sample_chunk(int n) { return n >= 9 ? 512 : 1 << n; }
+
+cudaError_t launch_sample(int dtype, const void *state, int n, uint64_t mask, uint64_t shots, uint64_t seed,
+                          double *partials, double *offsets, uint64_t *d_out, cudaStream_t s) {
+    const uint32_t chunk = (uint32_t)sample_chunk(n);
+    const uint32_t P = (uint32_t)((1ull << n) / chunk);
+    if (dtype == 0) k_sample_partials<float><<<P, 256, 0, s>>>(state, chunk, partials);
+    else k_sample_partials<double><<<P, 256, 0, s>>>(state, chunk, partials);
+    k_sample_scan<<<1, 1024, 0, s>>>(partials, P, offsets);
+    if (shots) {
+        const uint64_t blocks = std::min<uint64_t>((shots + 7) / 8, 152ull * 8);
+        if (dtype == 0)
+            k_sample_draw<float><<<(unsigned)blocks, 256, 0, s>>>(state, chunk, P, offsets, seed, shots, mask, d_out);
+        else
+            k_sample_draw<double><<<(unsigned)blocks, 256, 0, s>>>(state, chunk, P, offsets, seed, shots, mask, d_out);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,

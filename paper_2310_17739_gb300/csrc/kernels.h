@@ -198,5 +198,11 @@ int expect_blocks(int n);
 cudaError_t launch_expect(int dtype, const void *state, int n, const uint64_t *d_terms,
                           size_t n_terms, double *partials, double *d_out, cudaStream_t s);
 cudaError_t launch_set_basis(int dtype, void *state, int n, uint64_t index, cudaStream_t s);
+// Final-state shots (see qsim_sample): chunks of sample_chunk(n) consecutive
+// amplitudes; partials holds 2^n / chunk doubles, offsets one more, d_out
+// `shots` words.
+int sample_chunk(int n);
+cudaError_t launch_sample(int dtype, const void *state, int n, uint64_t mask, uint64_t shots, uint64_t seed,
+                          double *partials, double *offsets, uint64_t *d_out, cudaStream_t s);
 
 }  // namespace qsim

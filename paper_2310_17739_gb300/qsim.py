@@ -95,6 +95,7 @@ _SIGS = {
     "qsim_server_counts": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
                             ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i32),
     "qsim_server_now": ([_vp], _dbl),
+    "qsim_sample": ([_vp, _u64, _u64, _u64, _vp], _i32),
     "qsim_profile_start": ([_vp, _i32], _i32),
     "qsim_profile_read": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_u64), ctypes.POINTER(_dbl),
                            ctypes.POINTER(_dbl), ctypes.POINTER(_u64)], _i32),
@@ -322,6 +323,14 @@ class Sim:
         return _lib.qsim_sync(self.h)
 
     # -- sampled kernel timing
+    def sample(self, shots: int, seed: int = 0, mask: int | None = None) -> np.ndarray:
+        """Final-state shots without collapse (see qsim_sample): packed bits of `mask`
+        (default: every qubit) per shot."""
+        mask = (1 << self.n) - 1 if mask is None else int(mask)
+        out = np.zeros(max(int(shots), 1), dtype=np.uint64)
+        _check(_lib.qsim_sample(self.h, mask, int(shots), int(seed), _ptr(out)), self.h)
+        return out[: int(shots)]
+
     def profile_start(self, every: int):
         _check(_lib.qsim_profile_start(self.h, every), self.h)
 

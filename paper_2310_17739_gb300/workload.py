@@ -358,6 +358,39 @@ def config_large(seed=3, target_gates=115_000_000, n_meas=8) -> Circuit:
                        target_gates=target_gates, n_meas=n_meas)
 
 
+def projection_filter(n_sys, *, seed, blocks=8, trotter=4, theta_scale=0.4) -> Circuit:
+    """A synthetic projection filter in the shape of the paper's circuits: the
+    system qubits 0..n_sys-1 start in the uniform superposition (H on each);
+    each of `blocks` filter blocks puts the ancilla (qubit n_sys) in |+>, applies
+    the controlled evolution exp(2i sum_j theta_j Z_j) on ancilla |1> as
+    `trotter` slices of exp(-i (theta_j / trotter) Z_a Z_j) gadgets and
+    RZ(-2 theta_j / trotter) on qubit j, closes with H on the ancilla, asserts
+    the ancilla in |0> (assertion-mode measurement) and resets it.  The angles
+    theta_j ~ theta_scale * U(-1, 1) are in meta["thetas"]."""
+    rng = np.random.default_rng(seed)
+    thetas = theta_scale * rng.uniform(-1.0, 1.0, size=n_sys)
+    a = n_sys
+    rows = [(OP["H"], q, 0, 0.0) for q in range(n_sys)]
+    recs = [from_columns([r[0] for r in rows], [r[1] for r in rows], [r[2] for r in rows],
+                         [r[3] for r in rows])]
+    for _ in range(blocks):
+        rows = [(OP["H"], a, 0, 0.0)]
+        for _ in range(trotter):
+            for j in range(n_sys):
+                t = float(thetas[j]) / trotter
+                rows += gadget_rows(sorted([j, a]), "ZZ", t)
+                rows.append((OP["RZ"], j, 0, -2.0 * t))
+        rows.append((OP["H"], a, 0, 0.0))
+        recs.append(from_columns([r[0] for r in rows], [r[1] for r in rows], [r[2] for r in rows],
+                                 [r[3] for r in rows]))
+        m = np.zeros(2, dtype=GATE_DTYPE)
+        m[0]["op"], m[0]["q0"], m[0]["flags"] = OP["MEASURE"], a, 1
+        m[1]["op"], m[1]["q0"] = OP["RESET"], a
+        recs.append(m)
+    return Circuit(n_sys + 1, np.concatenate(recs), None, seed=seed, thetas=thetas, blocks=blocks,
+                   trotter=trotter)
+
+
 def config_batched(seed=4, n_param_sets=512, n_uneven=256, gates=20_000, n_terms=200,
                    n_set_gadgets=1600):
     """(i) n_param_sets parameter sets (theta ~ U(-pi, pi), set i drawn with seed

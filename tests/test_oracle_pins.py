@@ -440,3 +440,29 @@ def test_sample_born_statistics_and_special_states():
     u = np.full(1 << n, 0.25, dtype=np.complex128)
     counts = np.bincount(oracle.sample(u, n, 32000, seed=2).astype(np.int64), minlength=16)
     assert scipy.stats.chisquare(counts).pvalue > 1e-4
+
+
+# --------------------------------------------- projection filter (assertions) --
+def filter_closed_form(thetas, blocks):
+    """P(0) of each filter block and their product, from the system's uniform
+    superposition: the controlled phase on |x> is phi_x = 2 sum_j theta_j s_j
+    (s_j = +-1), block k keeps the weight cos^2(phi_x / 2) once more."""
+    n = thetas.size
+    x = np.arange(1 << n)
+    s = 1.0 - 2.0 * ((x[:, None] >> np.arange(n)[None, :]) & 1)
+    phi = 2.0 * (s * thetas[None, :]).sum(axis=1)
+    c2 = np.cos(phi / 2) ** 2
+    m = [np.mean(c2 ** k) for k in range(blocks + 1)]
+    return np.array([m[k] / m[k - 1] for k in range(1, blocks + 1)]), m[blocks]
+
+
+def test_projection_filter_assertions_follow_the_closed_form():
+    c = W.projection_filter(7, seed=11, blocks=5, trotter=3)
+    psi = oracle.basis_state(c.n)
+    r = oracle.run(psi, c.n, c.gates, seed=0)
+    assert r.status == 0
+    p0, prod = filter_closed_form(c.meta["thetas"], 5)
+    assert np.all(r.outcomes == 0)
+    assert np.abs(r.probs[0::2] - p0).max() < 1e-12       # the asserted P(0) of each block
+    assert np.all(r.probs[1::2] == 1.0)                    # the resets after an assertion
+    assert abs(np.prod(r.probs[0::2]) - prod) < 1e-12

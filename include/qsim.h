@@ -393,6 +393,27 @@ QSIM_API double qsim_server_now(const qsim_server *s);
 QSIM_API qsim_status qsim_prob_noalloc(const void *d_state, int n_qubits, qsim_dtype dtype, int qubit,
                                        void *stream, double *p0, double *p1);
 
+/* ------------------------------------------------------ OpenQASM 2.0 text --
+ * qsim_parse_qasm: the gate records of an OpenQASM 2.0 program (the paper's
+ * circuits are QASM files; Section "Simulator Framework", Table "Gates defined
+ * in IBM OpenQASM").  Read: OPENQASM 2.x; include (qelib1 is built in);
+ * qreg/creg (qubits numbered by declaration order, up to 64); the qelib1 gates
+ * id x y z h s sdg t tdg rx ry rz u1 p u2 u3 u U cx CX cy cz ch swap crx cry crz
+ * cu1 cp cu3 rxx rzz sx sxdg ccx cswap, applied to qubits or broadcast over
+ * whole registers of one size; parameter expressions (numbers, pi, + - * / ^,
+ * unary minus, sin cos tan exp ln sqrt); `gate` definitions (expanded in
+ * place); measure (-> a declared creg), reset, barrier (a full barrier).  Not
+ * read: opaque, if.  ccx and cswap become 1- and 2-qubit gates, sx and sxdg C1
+ * records; gate matrices and global phases are the library's (see the record
+ * definitions above).  Writes gates[0..*n_gates), mats[0..*n_mats) (doubles,
+ * for the C1 records) and *n_qubits.  Two-call use: with capacities too small
+ * it returns QSIM_E_INVAL after setting *n_gates and *n_mats.  Errors: a
+ * message "line L: ..." in err (err_cap bytes, NUL-terminated), QSIM_E_INVAL;
+ * QSIM_E_OOM when host memory runs out.  Host only. */
+QSIM_API qsim_status qsim_parse_qasm(const char *text, size_t len, qsim_gate *gates, size_t cap_gates,
+                                     size_t *n_gates, double *mats, size_t cap_mats, size_t *n_mats,
+                                     int *n_qubits, char *err, size_t err_cap);
+
 /* ------------------------------------------- host-only compiler inspection --
  * These run the host compiler only (no GPU needed).
  *

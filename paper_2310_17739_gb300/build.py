@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libqsim.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "qasm.cpp", "noalloc.cu"]
 HEADERS = ["kernels.h", "compiler.h"]
 
 

@@ -96,6 +96,8 @@ _SIGS = {
                             ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i32),
     "qsim_server_now": ([_vp], _dbl),
     "qsim_sample": ([_vp, _u64, _u64, _u64, _vp], _i32),
+    "qsim_parse_qasm": ([ctypes.c_char_p, _sz, _vp, _sz, ctypes.POINTER(_sz), _vp, _sz, ctypes.POINTER(_sz),
+                         ctypes.POINTER(_i32), ctypes.c_char_p, _sz], _i32),
     "qsim_profile_start": ([_vp, _i32], _i32),
     "qsim_profile_read": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_u64), ctypes.POINTER(_dbl),
                            ctypes.POINTER(_dbl), ctypes.POINTER(_u64)], _i32),
@@ -533,6 +535,24 @@ def fuse(n, gates, mats=None, dtype=C64, **cfg):
             M = md[off: off + 2 * d * d].view(np.complex128).reshape(d, d).copy()
             out.append((k, [int(x) for x in oq[6 * i: 6 * i + k]], M))
     return out
+
+
+def parse_qasm(text):
+    """OpenQASM 2.0 text -> (n_qubits, gate records, matrix doubles); see qsim_parse_qasm."""
+    raw = text.encode() if isinstance(text, str) else bytes(text)
+    ng, nm, nq = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+    err = ctypes.create_string_buffer(512)
+    st = _lib.qsim_parse_qasm(raw, len(raw), None, 0, ctypes.byref(ng), None, 0, ctypes.byref(nm),
+                              ctypes.byref(nq), err, 512)
+    if st != OK and not (st == E_INVAL and err.value == b"output capacity too small"):
+        raise QsimError(st, err.value.decode(errors="replace"))
+    g = np.zeros(max(ng.value, 1), dtype=GATE_DTYPE)
+    m = np.zeros(max(nm.value, 1), dtype=np.float64)
+    st = _lib.qsim_parse_qasm(raw, len(raw), _ptr(g), g.size, ctypes.byref(ng), _ptr(m), m.size,
+                              ctypes.byref(nm), ctypes.byref(nq), err, 512)
+    if st != OK:
+        raise QsimError(st, err.value.decode(errors="replace"))
+    return nq.value, g[: ng.value], m
 
 
 def schedule(n, gates, mats=None, dtype=C64, with_basis=False, **cfg):

@@ -856,7 +856,8 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             // a complex64 rotation-only pass runs as register segments, which
             // hold a rotation whose tile coordinates span at most 5 bits: a
             // wider one (an X mask already in the span) waits for a later pass
-            if (ok && reg_candidate && only_rot && o.pauli() && V.contains(o.xm) &&
+            // (the pass's first op is always taken, so every pass makes progress)
+            if (ok && i != f && reg_candidate && only_rot && o.pauli() && V.contains(o.xm) &&
                 popc(V.coords(o.xm)) > 5)
                 ok = false;
             if (ok && (Q & blocked_p)) {

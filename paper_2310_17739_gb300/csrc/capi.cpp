@@ -381,12 +381,28 @@ struct qsim_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
     // live programs compiled on this context (released and orphaned by qsim_destroy)
     std::vector<qsim_program *> programs;
+    uint64_t cfg_gen = 0;                 // bumped by qsim_set_config (invalidates program graphs)
+    cudaStream_t cap_stream = nullptr;    // private stream for graph capture (nothing runs on it)
+};
+
+// A run of consecutive tile passes of one chunk (no measurement between
+// them), replayed as one CUDA graph launch once captured.
+struct PassRun {
+    size_t first = 0, end = 0;        // pass indices [first, end) in DevChunk::passes
+    uint64_t launches = 0;            // tile-pass launches in it
+    double flops = 0;                 // algorithmic flops of those launches
+    cudaGraphExec_t exec = nullptr;
 };
 
 struct qsim_program {
     qsim_ctx *owner = nullptr;
     std::vector<DevChunk> chunks;
     qsim_program_info info{};
+    // graph replay (qsim_config::graphs): per chunk, its runs of tile passes
+    mutable uint64_t runs_done = 0;   // completed qsim_run calls
+    mutable bool graphs_ready = false, graphs_failed = false;
+    mutable uint64_t graph_gen = 0;   // ctx cfg_gen the graphs were captured under
+    mutable std::vector<std::vector<PassRun>> runs;
 };
 
 namespace {
@@ -583,12 +599,27 @@ cudaError_t profile_close(qsim_ctx *c) {
     return e;
 }
 
+// Threads per block of the generic tile pass: 512 for complex64 rotation
+// passes (more warps in flight); dense C2 passes and complex128 keep 256 (their
+// 512-thread builds are capped at 64 registers and lose more to spills than
+// they gain).
+int tile_threads(const qsim_ctx *c) {
+    return c->cfg.threads ? c->cfg.threads : (c->dtype == QSIM_C64 && c->cfg.fusion == 2 ? 512 : 256);
+}
+
+// One tile pass (register-segment or generic) on stream s.
+cudaError_t launch_tile(qsim_ctx *c, const DevChunk &dc, const Pass &p, int threads, cudaStream_t s) {
+    const uint64_t *basis = dc.bvec.data() + p.basis;
+    if (p.reg)
+        return qsim::launch_rot_pass(c->state, c->n, dc.m, p.tile, basis, dc.d_ops + p.first, p.count, dc.d_mats,
+                                     (uint32_t)p.mat_first, p.mat_count, p.scale, c->ctl, s);
+    return qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile, basis,
+                                  dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first, p.mat_count,
+                                  c->ctl, s);
+}
+
 qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
-    // 512 threads per tile for complex64 rotation passes (more warps in flight);
-    // dense C2 passes and complex128 keep 256 (their 512-thread builds are capped
-    // at 64 registers and lose more to spills than they gain)
-    const int threads = c->cfg.threads ? c->cfg.threads
-                                       : (c->dtype == QSIM_C64 && c->cfg.fusion == 2 ? 512 : 256);
+    const int threads = tile_threads(c);
     if (dc.resident) {
         qsim_status s = ensure_log(c, c->log_n + dc.measurements);
         if (s != QSIM_OK) return s;
@@ -625,8 +656,8 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
             c->prof_open = true;
             c->prof_in_window = 0;
         }
-        const uint64_t *basis = dc.bvec.data() + p.basis;
         if (p.reg && c->cfg.persistent && dc.m <= 13) {
+            const uint64_t *basis = dc.bvec.data() + p.basis;
             if (!c->tile_ctr) {
                 c->tile_ctr = (unsigned long long *)dalloc(c, sizeof(unsigned long long));
                 if (!c->tile_ctr) return fail(c, QSIM_E_OOM, "tile counter allocation failed");
@@ -639,16 +670,8 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
                                      c->tile_ctr, c->tile_base, &grid, c->stream),
                "persistent rotation pass launch");
             c->tile_base += (1ull << (c->n - dc.m)) + grid;
-        } else if (p.reg)
-            CK(qsim::launch_rot_pass(c->state, c->n, dc.m, p.tile, basis, dc.d_ops + p.first, p.count,
-                                     dc.d_mats, (uint32_t)p.mat_first, p.mat_count, p.scale, c->ctl,
-                                     c->stream),
-               "rotation pass launch");
-        else
-            CK(qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile, basis,
-                                      dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
-                                      p.mat_count, c->ctl, c->stream),
-               "tile pass launch");
+        } else
+            CK(launch_tile(c, dc, p, threads, c->stream), p.reg ? "rotation pass launch" : "tile pass launch");
         if (c->prof_open) {
             c->prof_in_window++;
             c->prof_flops += (double)p.fpa * (double)(1ull << c->n);
@@ -657,6 +680,120 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
                 CK(profile_close(c), "profile event");
         }
         c->prof_launches++;
+    }
+    return QSIM_OK;
+}
+
+// ----------------------------------------------------------- graph replay --
+// A compiled program replayed by qsim_run: every run of tile passes between two
+// measurements is captured once as a CUDA graph (kernel nodes joined by the
+// same programmatic dependencies as the stream launches) and then replayed
+// with one graph launch, which saves the per-launch cost of stream launches.
+constexpr uint64_t kGraphMaxPasses = 1ull << 21;
+
+void destroy_graphs(qsim_ctx *c, const qsim_program *p) {
+    bool any = false;
+    for (auto &rs : p->runs)
+        for (auto &r : rs) any = any || r.exec;
+    if (any) cudaStreamSynchronize(c->stream);  // no launch of them may be pending
+    for (auto &rs : p->runs)
+        for (auto &r : rs)
+            if (r.exec) cudaGraphExecDestroy(r.exec);
+    p->runs.clear();
+    p->graphs_ready = false;
+    cudaGetLastError();
+}
+
+// Capture on a private stream (capture enqueues nothing).  On any failure the
+// program is marked and falls back to launching its passes one by one.
+qsim_status build_graphs(qsim_ctx *c, const qsim_program *p) {
+    destroy_graphs(c, p);
+    uint64_t total = 0;
+    for (const DevChunk &dc : p->chunks)
+        if (!dc.resident)
+            for (const Pass &ps : dc.passes) total += !ps.ev && ps.count;
+    if (total > kGraphMaxPasses) {
+        p->graphs_failed = true;
+        return QSIM_OK;
+    }
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    const int threads = tile_threads(c);
+    p->runs.assign(p->chunks.size(), {});
+    for (size_t ci = 0; ci < p->chunks.size(); ci++) {
+        const DevChunk &dc = p->chunks[ci];
+        if (dc.resident) continue;
+        for (size_t i = 0; i < dc.passes.size();) {
+            if (dc.passes[i].ev) {
+                i++;
+                continue;
+            }
+            PassRun r;
+            r.first = i;
+            for (; i < dc.passes.size() && !dc.passes[i].ev; i++)
+                if (dc.passes[i].count) {
+                    r.launches++;
+                    r.flops += (double)dc.passes[i].fpa * (double)(1ull << c->n);
+                }
+            r.end = i;
+            if (r.launches) {
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (size_t k = r.first; e == cudaSuccess && k < r.end; k++)
+                        if (dc.passes[k].count) e = launch_tile(c, dc, dc.passes[k], threads, c->cap_stream);
+                    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&r.exec, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    r.exec = nullptr;
+                    p->runs[ci].push_back(r);
+                    destroy_graphs(c, p);
+                    p->graphs_failed = true;
+                    return QSIM_OK;
+                }
+            }
+            p->runs[ci].push_back(r);
+        }
+    }
+    p->graphs_ready = true;
+    return QSIM_OK;
+}
+
+// launch_chunk with each run of tile passes as one graph launch (a profiling
+// window, when sampling is on, spans exactly one graph launch).
+qsim_status run_chunk_graphs(qsim_ctx *c, const DevChunk &dc, const std::vector<PassRun> &rs) {
+    size_t ri = 0;
+    for (size_t i = 0; i < dc.passes.size();) {
+        const Pass &ps = dc.passes[i];
+        if (ps.ev) {
+            CK(profile_close(c), "profile event");
+            qsim_status s = launch_measure(c, (int)ps.q, ps.flags, ps.ev == qsim::EV_RESET, c->seed);
+            if (s != QSIM_OK) return s;
+            i++;
+            continue;
+        }
+        if (ri >= rs.size() || rs[ri].first != i) return fail(c, QSIM_E_STATE, "graph runs out of step");
+        const PassRun &r = rs[ri++];
+        if (r.exec) {
+            const bool win = c->prof_every > 0;
+            if (win) CK(profile_close(c), "profile event");
+            const bool open = win && c->prof_used < c->prof_ev.size();
+            if (open) {
+                CK(cudaEventRecord(c->prof_ev[c->prof_used].first, c->stream), "profile event");
+                c->prof_open = true;
+            }
+            CK(cudaGraphLaunch(r.exec, c->stream), "graph launch");
+            if (open) {
+                c->prof_in_window = (uint32_t)r.launches;
+                c->prof_flops += r.flops;
+                c->prof_bytes += 2.0 * (double)c->state_bytes * (double)r.launches;
+                CK(profile_close(c), "profile event");
+            }
+            c->prof_launches += r.launches;
+        }
+        i = r.end;
     }
     return QSIM_OK;
 }
@@ -822,6 +959,7 @@ qsim_status qsim_destroy(qsim_ctx *c) {
     cudaSetDevice(c->device);
     // programs still alive release their device buffers now and become orphans
     for (qsim_program *p : c->programs) {
+        destroy_graphs(c, p);
         for (auto &dc : p->chunks) release_chunk(c, dc);
         p->owner = nullptr;
     }
@@ -837,6 +975,7 @@ qsim_status qsim_destroy(qsim_ctx *c) {
         cudaFreeHost(s.host);
     }
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto &e : c->prof_ev) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -870,7 +1009,9 @@ qsim_status qsim_set_config(qsim_ctx *c, const qsim_config *cfg) {
     if (cfg->chunk_gates < 0 || cfg->lookahead < 0 || cfg->compile_threads < 0)
         return fail(c, QSIM_E_INVAL, "negative size");
     if (cfg->persistent != 0 && cfg->persistent != 1) return fail(c, QSIM_E_INVAL, "persistent must be 0 or 1");
+    if (cfg->graphs < 0 || cfg->graphs > 2) return fail(c, QSIM_E_INVAL, "graphs must be 0, 1 or 2");
     c->cfg = qsim::config_from(cfg);
+    c->cfg_gen++;
     return QSIM_OK;
 }
 
@@ -943,10 +1084,21 @@ qsim_status qsim_run(qsim_ctx *c, const qsim_program *p) {
     qsim_status s = check_usable(c);
     if (s != QSIM_OK) return s;
     if (!p || p->owner != c) return fail(c, QSIM_E_INVAL, "program does not belong to this context");
-    for (const DevChunk &dc : p->chunks) {
-        s = launch_chunk(c, dc);
+    const int mode = c->cfg.graphs;
+    const bool want = mode != 2 && !c->cfg.persistent && !p->graphs_failed && (p->runs_done >= 1 || mode == 1);
+    if (!want && p->graphs_ready) destroy_graphs(c, p);
+    if (want && (!p->graphs_ready || p->graph_gen != c->cfg_gen)) {
+        s = build_graphs(c, p);
+        if (s != QSIM_OK) return s;
+        p->graph_gen = c->cfg_gen;
+    }
+    const bool use = want && p->graphs_ready;
+    for (size_t ci = 0; ci < p->chunks.size(); ci++) {
+        const DevChunk &dc = p->chunks[ci];
+        s = use && !dc.resident ? run_chunk_graphs(c, dc, p->runs[ci]) : launch_chunk(c, dc);
         if (s != QSIM_OK) return s;
     }
+    p->runs_done++;
     return QSIM_OK;
 }
 
@@ -961,6 +1113,7 @@ qsim_status qsim_program_free(qsim_program *p) {
     if (p->owner) {  // an orphan (its context destroyed) holds no device memory any more
         qsim_ctx *c = p->owner;
         cudaSetDevice(c->device);
+        destroy_graphs(c, p);
         for (auto &dc : p->chunks) release_chunk(c, dc);
         c->programs.erase(std::remove(c->programs.begin(), c->programs.end(), p), c->programs.end());
     }

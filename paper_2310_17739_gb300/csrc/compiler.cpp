@@ -388,6 +388,7 @@ Config config_from(const qsim_config *c) {
     k.lookahead = c->lookahead;
     k.compile_threads = c->compile_threads;
     k.persistent = c->persistent;
+    k.graphs = c->graphs;
     return k;
 }
 
@@ -401,6 +402,7 @@ void config_to(const Config &c, qsim_config *o) {
     o->lookahead = c.lookahead;
     o->compile_threads = c.compile_threads;
     o->persistent = c.persistent;
+    o->graphs = c.graphs;
 }
 
 static int max_tile_bits(qsim_dtype dt) { return dt == QSIM_C64 ? 14 : 13; }

@@ -151,6 +151,7 @@ struct Config {
     int lookahead = 0;
     int compile_threads = 0;
     int persistent = 0;
+    int graphs = 0;
 };
 
 Config config_from(const qsim_config *c);

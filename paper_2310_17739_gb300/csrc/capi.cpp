@@ -690,6 +690,7 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
 // same programmatic dependencies as the stream launches) and then replayed
 // with one graph launch, which saves the per-launch cost of stream launches.
 constexpr uint64_t kGraphMaxPasses = 1ull << 21;
+constexpr size_t kApplyGraphMin = 256;  // qsim_apply: chunks with fewer tile passes launch them directly
 
 void destroy_graphs(qsim_ctx *c, const qsim_program *p) {
     bool any = false;
@@ -704,8 +705,58 @@ void destroy_graphs(qsim_ctx *c, const qsim_program *p) {
     cudaGetLastError();
 }
 
-// Capture on a private stream (capture enqueues nothing).  On any failure the
-// program is marked and falls back to launching its passes one by one.
+// Capture every run of tile passes of one chunk as a CUDA graph, on a private
+// stream (capture enqueues nothing).  Returns false, with no graph left, if
+// any capture or instantiation fails.
+bool capture_chunk(qsim_ctx *c, const DevChunk &dc, std::vector<PassRun> &rs) {
+    rs.clear();
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->cap_stream = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    const int threads = tile_threads(c);
+    bool ok = true;
+    for (size_t i = 0; ok && i < dc.passes.size();) {
+        if (dc.passes[i].ev) {
+            i++;
+            continue;
+        }
+        PassRun r;
+        r.first = i;
+        for (; i < dc.passes.size() && !dc.passes[i].ev; i++)
+            if (dc.passes[i].count) {
+                r.launches++;
+                r.flops += (double)dc.passes[i].fpa * (double)(1ull << c->n);
+            }
+        r.end = i;
+        if (r.launches) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (size_t k = r.first; e == cudaSuccess && k < r.end; k++)
+                    if (dc.passes[k].count) e = launch_tile(c, dc, dc.passes[k], threads, c->cap_stream);
+                const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&r.exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                r.exec = nullptr;
+                ok = false;
+            }
+        }
+        rs.push_back(r);
+    }
+    if (!ok) {
+        for (auto &r : rs)
+            if (r.exec) cudaGraphExecDestroy(r.exec);
+        rs.clear();
+        cudaGetLastError();
+    }
+    return ok;
+}
+
 qsim_status build_graphs(qsim_ctx *c, const qsim_program *p) {
     destroy_graphs(c, p);
     uint64_t total = 0;
@@ -716,45 +767,13 @@ qsim_status build_graphs(qsim_ctx *c, const qsim_program *p) {
         p->graphs_failed = true;
         return QSIM_OK;
     }
-    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
-    const int threads = tile_threads(c);
     p->runs.assign(p->chunks.size(), {});
     for (size_t ci = 0; ci < p->chunks.size(); ci++) {
-        const DevChunk &dc = p->chunks[ci];
-        if (dc.resident) continue;
-        for (size_t i = 0; i < dc.passes.size();) {
-            if (dc.passes[i].ev) {
-                i++;
-                continue;
-            }
-            PassRun r;
-            r.first = i;
-            for (; i < dc.passes.size() && !dc.passes[i].ev; i++)
-                if (dc.passes[i].count) {
-                    r.launches++;
-                    r.flops += (double)dc.passes[i].fpa * (double)(1ull << c->n);
-                }
-            r.end = i;
-            if (r.launches) {
-                cudaGraph_t g = nullptr;
-                cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    for (size_t k = r.first; e == cudaSuccess && k < r.end; k++)
-                        if (dc.passes[k].count) e = launch_tile(c, dc, dc.passes[k], threads, c->cap_stream);
-                    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&r.exec, g, 0);
-                if (g) cudaGraphDestroy(g);
-                if (e != cudaSuccess) {
-                    r.exec = nullptr;
-                    p->runs[ci].push_back(r);
-                    destroy_graphs(c, p);
-                    p->graphs_failed = true;
-                    return QSIM_OK;
-                }
-            }
-            p->runs[ci].push_back(r);
+        if (p->chunks[ci].resident) continue;
+        if (!capture_chunk(c, p->chunks[ci], p->runs[ci])) {
+            destroy_graphs(c, p);
+            p->graphs_failed = true;
+            return QSIM_OK;
         }
     }
     p->graphs_ready = true;
@@ -1043,7 +1062,22 @@ qsim_status qsim_apply(qsim_ctx *c, const qsim_gate *g, size_t ng, const double 
     return compile_chunks(c, g, ng, mats, nm, [&](const Packed &pk) -> qsim_status {
         DevChunk dc;
         qsim_status st = upload_chunk(c, pk, dc);
-        if (st == QSIM_OK) st = launch_chunk(c, dc);
+        if (st == QSIM_OK) {
+            // a long chunk runs as graph launches (capture and instantiation cost
+            // the host about what stream launches would; the device saves the
+            // per-launch cost)
+            size_t tile_passes = 0;
+            for (const Pass &ps : dc.passes) tile_passes += !ps.ev && ps.count;
+            std::vector<PassRun> rs;
+            if (c->cfg.graphs != 2 && !c->cfg.persistent && !dc.resident && tile_passes >= kApplyGraphMin &&
+                capture_chunk(c, dc, rs)) {
+                st = run_chunk_graphs(c, dc, rs);
+                for (auto &r : rs)  // released when their launches complete
+                    if (r.exec) cudaGraphExecDestroy(r.exec);
+            } else {
+                st = launch_chunk(c, dc);
+            }
+        }
         release_chunk(c, dc);  // stream-ordered: freed after the launches above
         return st;
     });

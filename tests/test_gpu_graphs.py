@@ -116,3 +116,28 @@ def test_program_freed_after_graph_replay_and_context_destroyed_first():
     p1.free()
     sim.close()
     p2.free()
+
+
+def test_apply_long_chunks_as_graphs_matches_stream_launches():
+    """qsim_apply runs a chunk of >= 256 tile passes as graph launches (the
+    graphs released as soon as they are launched): same state and outcomes as
+    launching every pass, and the oracle's outcomes."""
+    n = 16
+    c = W.ucc_circuit(n, seed=53, n_gadgets=None, w_lo=2, w_hi=6, theta="uniform", target_gates=40000, n_meas=4)
+    res = []
+    for graphs in (2, 0):
+        sim = qs.Sim(n, "c64", seed=5, config=dict(fusion=2, tile_bits=12, graphs=graphs))
+        prog = sim.compile(c.gates)
+        passes = prog.info()["passes"]
+        prog.free()
+        sim.apply(c.gates, c.mats)
+        assert sim.sync() == 0
+        res.append((sim.state(), sim.outcomes()[0]))
+        sim.close()
+    assert passes >= 256
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    psi = oracle.basis_state(n)
+    r = oracle.run(psi, n, c.gates, c.mats, seed=5)
+    assert np.array_equal(res[1][1], r.outcomes)
+    assert 1 - H.fidelity(psi, res[1][0]) <= 1e-5

@@ -609,9 +609,12 @@ def run_serving(args):
     warm = qs.Server(slots=8, dtype="c64", config=dict(fusion=fusion))
     wid = [warm.submit(c.n, c.gates[:2000], seed=1) for c in pool[:8]]
     done = 0
-    while done < len(wid):
+    t_warm = time.perf_counter()
+    while done < len(wid) and time.perf_counter() - t_warm < 120:
         done += len(warm.poll())
         time.sleep(0.01)
+    if done < len(wid):
+        print(f"serving warm-up: {done} of {len(wid)} requests done after 120 s", file=sys.stderr, flush=True)
     warm.close()
 
     srv = qs.Server(slots=args.slots, dtype="c64", config=dict(fusion=fusion))
@@ -621,6 +624,7 @@ def run_serving(args):
     t_start = srv.now()
     k = 0
     drain_deadline = T + args.serve_seconds  # stop waiting for stragglers after this
+    next_report = 10.0
     while True:
         now = srv.now() - t_start
         while k < len(arrivals) and arrivals[k][0] <= now:
@@ -633,6 +637,9 @@ def run_serving(args):
             results[r["id"]] = r
         if k >= len(arrivals) and (len(results) >= len(arrivals) or now > drain_deadline):
             break
+        if now >= next_report:  # progress on stderr (the result line stays on stdout)
+            print(f"serving t={now:.0f}s submitted={k} completed={len(results)}", file=sys.stderr, flush=True)
+            next_report += 10.0
         time.sleep(0.0005)
     t_end = srv.now() - t_start
     clk = clocks.stop()

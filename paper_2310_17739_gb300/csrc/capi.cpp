@@ -817,6 +817,23 @@ qsim_status run_chunk_graphs(qsim_ctx *c, const DevChunk &dc, const std::vector<
     return QSIM_OK;
 }
 
+// A chunk launched once by qsim_apply: a long one runs as graph
+// launches (capture and instantiation cost the host about what stream launches
+// would; the device saves the per-launch cost), released right after launch
+// (an executable graph still in flight is freed when it completes).
+qsim_status launch_chunk_once(qsim_ctx *c, const DevChunk &dc) {
+    size_t tile_passes = 0;
+    for (const Pass &ps : dc.passes) tile_passes += !ps.ev && ps.count;
+    std::vector<PassRun> rs;
+    if (c->cfg.graphs == 2 || c->cfg.persistent || dc.resident || tile_passes < kApplyGraphMin ||
+        !capture_chunk(c, dc, rs))
+        return launch_chunk(c, dc);
+    const qsim_status st = run_chunk_graphs(c, dc, rs);
+    for (auto &r : rs)
+        if (r.exec) cudaGraphExecDestroy(r.exec);
+    return st;
+}
+
 size_t chunk_size(const qsim_ctx *c) {
     return c->cfg.chunk_gates > 0 ? (size_t)c->cfg.chunk_gates : ((size_t)1 << 20);
 }
@@ -1062,22 +1079,7 @@ qsim_status qsim_apply(qsim_ctx *c, const qsim_gate *g, size_t ng, const double 
     return compile_chunks(c, g, ng, mats, nm, [&](const Packed &pk) -> qsim_status {
         DevChunk dc;
         qsim_status st = upload_chunk(c, pk, dc);
-        if (st == QSIM_OK) {
-            // a long chunk runs as graph launches (capture and instantiation cost
-            // the host about what stream launches would; the device saves the
-            // per-launch cost)
-            size_t tile_passes = 0;
-            for (const Pass &ps : dc.passes) tile_passes += !ps.ev && ps.count;
-            std::vector<PassRun> rs;
-            if (c->cfg.graphs != 2 && !c->cfg.persistent && !dc.resident && tile_passes >= kApplyGraphMin &&
-                capture_chunk(c, dc, rs)) {
-                st = run_chunk_graphs(c, dc, rs);
-                for (auto &r : rs)  // released when their launches complete
-                    if (r.exec) cudaGraphExecDestroy(r.exec);
-            } else {
-                st = launch_chunk(c, dc);
-            }
-        }
+        if (st == QSIM_OK) st = launch_chunk_once(c, dc);
         release_chunk(c, dc);  // stream-ordered: freed after the launches above
         return st;
     });
@@ -2020,6 +2022,7 @@ void ctx_free_async(qsim_ctx *c) {
         cudaEventDestroy(s.done);
         cudaFreeHost(s.host);
     }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;  // h_ctl is borrowed from the slot
 }
 

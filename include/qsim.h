@@ -139,13 +139,17 @@ typedef struct {
  * persistent  1: register-segment rotation passes (m <= 13) run as resident
  *          blocks that take tiles from a device counter and prefetch the next
  *          tile while computing the current one; 0: one block per tile.
- * graphs   how qsim_run replays a compiled program: 0 = each run of tile
- *          passes between two measurements is captured once as a CUDA graph
- *          when the program is run for the second time (programs of up to
- *          2^21 tile passes; ~2.7 KB of device memory per pass) and replayed
- *          as one graph launch from then on; 1 = captured at the first run;
- *          2 = never (every pass launched from the host).  Graphs are rebuilt
- *          after qsim_set_config; persistent = 1 never uses them.
+ * graphs   CUDA-graph launches of tile passes.  qsim_run: 0 = each run of
+ *          tile passes between two measurements of a compiled program is
+ *          captured once as a CUDA graph when the program is run for the
+ *          second time (programs of up to 2^21 tile passes; ~2.7 KB of device
+ *          memory per pass) and replayed as one graph launch from then on;
+ *          1 = captured at the first run.  qsim_apply (0 or 1): a chunk of
+ *          >= 256 tile passes is captured and launched as graphs, which are
+ *          destroyed once their launches have completed.  2 = never (every
+ *          pass launched from the host).  Graphs are rebuilt after
+ *          qsim_set_config; persistent = 1 never uses them.  The server
+ *          launches its requests' passes from the host.
  */
 typedef struct {
     int32_t fusion;

@@ -383,6 +383,8 @@ struct qsim_ctx {
     std::vector<qsim_program *> programs;
     uint64_t cfg_gen = 0;                 // bumped by qsim_set_config (invalidates program graphs)
     cudaStream_t cap_stream = nullptr;    // private stream for graph capture (nothing runs on it)
+    // graphs launched by qsim_apply, destroyed once the event after them has completed
+    std::deque<std::pair<cudaEvent_t, std::vector<cudaGraphExec_t>>> graph_retire;
 };
 
 // A run of consecutive tile passes of one chunk (no measurement between
@@ -518,10 +520,13 @@ qsim_status check_usable(qsim_ctx *c) {
 }
 
 // Synchronise, read the control block, report deferred device failures.
+void reap_graphs(qsim_ctx *c, bool wait);
+
 qsim_status sync_read(qsim_ctx *c) {
     CK(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(MeasCtl), cudaMemcpyDeviceToHost, c->stream),
        "control readback");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    reap_graphs(c, true);
     if (c->h_ctl->status == QSIM_E_ZEROPROB)
         return fail(c, QSIM_E_ZEROPROB,
                     "assertion-mode measurement #" + std::to_string(c->h_ctl->fail_log) +
@@ -817,11 +822,26 @@ qsim_status run_chunk_graphs(qsim_ctx *c, const DevChunk &dc, const std::vector<
     return QSIM_OK;
 }
 
-// A chunk launched once by qsim_apply: a long one runs as graph
-// launches (capture and instantiation cost the host about what stream launches
-// would; the device saves the per-launch cost), released right after launch
-// (an executable graph still in flight is freed when it completes).
+// A chunk launched once by qsim_apply: a long one runs as graph launches
+// (capture and instantiation cost the host about what stream launches would;
+// the device saves the per-launch cost); the graphs are destroyed once an event
+// recorded after them has completed.
+// Destroy the graphs of qsim_apply whose launches have completed (all of them,
+// waiting, when `wait`).
+void reap_graphs(qsim_ctx *c, bool wait) {
+    while (!c->graph_retire.empty()) {
+        auto &f = c->graph_retire.front();
+        if (wait) cudaEventSynchronize(f.first);
+        else if (cudaEventQuery(f.first) != cudaSuccess) break;
+        for (cudaGraphExec_t g : f.second) cudaGraphExecDestroy(g);
+        cudaEventDestroy(f.first);
+        c->graph_retire.pop_front();
+    }
+    cudaGetLastError();  // cudaErrorNotReady from the query
+}
+
 qsim_status launch_chunk_once(qsim_ctx *c, const DevChunk &dc) {
+    reap_graphs(c, false);
     size_t tile_passes = 0;
     for (const Pass &ps : dc.passes) tile_passes += !ps.ev && ps.count;
     std::vector<PassRun> rs;
@@ -829,8 +849,19 @@ qsim_status launch_chunk_once(qsim_ctx *c, const DevChunk &dc) {
         !capture_chunk(c, dc, rs))
         return launch_chunk(c, dc);
     const qsim_status st = run_chunk_graphs(c, dc, rs);
+    std::vector<cudaGraphExec_t> ex;
     for (auto &r : rs)
-        if (r.exec) cudaGraphExecDestroy(r.exec);
+        if (r.exec) ex.push_back(r.exec);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(ev, c->stream) == cudaSuccess) {
+        c->graph_retire.emplace_back(ev, std::move(ex));
+    } else {  // no event: wait for the stream before destroying them
+        cudaGetLastError();
+        if (ev) cudaEventDestroy(ev);
+        cudaStreamSynchronize(c->stream);
+        for (cudaGraphExec_t g : ex) cudaGraphExecDestroy(g);
+    }
     return st;
 }
 
@@ -994,6 +1025,7 @@ qsim_status qsim_destroy(qsim_ctx *c) {
     if (!c) return QSIM_OK;
     cudaSetDevice(c->device);
     // programs still alive release their device buffers now and become orphans
+    reap_graphs(c, true);
     for (qsim_program *p : c->programs) {
         destroy_graphs(c, p);
         for (auto &dc : p->chunks) release_chunk(c, dc);

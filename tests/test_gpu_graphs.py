@@ -120,7 +120,7 @@ def test_program_freed_after_graph_replay_and_context_destroyed_first():
 
 def test_apply_long_chunks_as_graphs_matches_stream_launches():
     """qsim_apply runs a chunk of >= 256 tile passes as graph launches (the
-    graphs released as soon as they are launched): same state and outcomes as
+    graphs released once their launches complete): same state and outcomes as
     launching every pass, and the oracle's outcomes."""
     n = 16
     c = W.ucc_circuit(n, seed=53, n_gadgets=None, w_lo=2, w_hi=6, theta="uniform", target_gates=40000, n_meas=4)

@@ -52,7 +52,8 @@ def parse():
                     help="-1: autotune (paper fusion, k-qubit merge, Pauli-gadget rotations); "
                          "0/1/2 force a fusion level")
     ap.add_argument("--profile-every", type=int, default=128,
-                    help="tile-pass timing windows of 16 launches, one every this many launches")
+                    help="tile-pass timing windows (a graph launch of a run of passes, or up to 16 "
+                         "stream launches), one every this many launches")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

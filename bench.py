@@ -666,6 +666,23 @@ def run_serving(args):
             fl_cache[pi] = (8 * n_rot + sum(8 << o[0] for o in dense)) * (1 << c.n)
         return fl_cache[pi]
     flops = sum(req_flops(meta[i][0]) for i in results)
+    # kernel launches of the served requests: k_set_basis, then one resident
+    # kernel (n <= 14) or every tile pass plus k_prob + k_collapse per
+    # measurement, then k_expect + k_expect_final
+    ln_cache = {}
+
+    def req_launches(pi):
+        if pi not in ln_cache:
+            c = pool[pi]
+            if c.n <= 14:
+                ln_cache[pi] = 4
+            else:
+                ps = qs.schedule(c.n, c.gates, dtype=qs.C64, fusion=fusion)
+                tiles = sum(1 for p in ps if p[0] and p[2])
+                events = sum(1 for p in ps if not p[0])
+                ln_cache[pi] = 1 + tiles + 2 * events + 2
+        return ln_cache[pi]
+    launches = sum(req_launches(meta[i][0]) for i in results)
     tflops = flops / window / 1e12
     statuses = {}
     for r in results.values():
@@ -697,7 +714,7 @@ def run_serving(args):
         "unfinished_at_deadline": len(arrivals) - completed,
         "offered_gates_per_s": offered_gates / T, "served_gates_per_s": gates_done / window,
         "saturated": bool(offered_gates / T > 1.05 * gates_done / window),
-        "gpu_launches": None,
+        "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": tflops / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",

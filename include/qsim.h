@@ -132,7 +132,10 @@ typedef struct {
  *          which also lets complex64 rotation passes run as register segments
  *          (2^(m-5) threads of 32 amplitudes).
  * chunk_gates  qsim_apply compiles and launches the stream in chunks of this
- *          many gates, overlapping host compilation with device work; 0 = 2^20.
+ *          many gates, overlapping host compilation with device work; 0 = a
+ *          first chunk of 2^16 gates, each next one twice as long up to 2^20
+ *          (the device starts sooner).  Every chunk ends with a Pauli-frame
+ *          flush, so chunking changes rounding only.
  * lookahead  how many fused ops the pass scheduler may scan past an op that
  *          does not fit, pulling later ops on disjoint qubits forward; 0 = 64.
  * compile_threads  host threads compiling chunks ahead of the launcher; 0 = auto.

@@ -865,8 +865,18 @@ qsim_status launch_chunk_once(qsim_ctx *c, const DevChunk &dc) {
     return st;
 }
 
-size_t chunk_size(const qsim_ctx *c) {
-    return c->cfg.chunk_gates > 0 ? (size_t)c->cfg.chunk_gates : ((size_t)1 << 20);
+// Chunk boundaries over ng gate records: chunk_gates each when set; by default
+// 2^16 gates first, doubling up to 2^20, so that the device starts on the first
+// chunk while the host still compiles the later, larger ones.
+std::vector<size_t> chunk_bounds(const qsim_ctx *c, size_t ng) {
+    std::vector<size_t> b{0};
+    size_t C = c->cfg.chunk_gates > 0 ? (size_t)c->cfg.chunk_gates : ((size_t)1 << 16);
+    const size_t cap = c->cfg.chunk_gates > 0 ? C : ((size_t)1 << 20);
+    while (b.back() < ng) {
+        b.push_back(std::min(ng, b.back() + C));
+        C = std::min(cap, 2 * C);
+    }
+    return b;
 }
 
 // Register-segment layout for rotation passes: single-state launches with the
@@ -884,8 +894,8 @@ int compile_threads(const qsim_ctx *c) {
 template <class Sink>
 qsim_status compile_chunks(qsim_ctx *c, const qsim_gate *g, size_t ng, const double *mats,
                            size_t nm, Sink sink) {
-    const size_t C = chunk_size(c);
-    const size_t nchunks = ng ? (ng + C - 1) / C : 0;
+    const std::vector<size_t> bounds = chunk_bounds(c, ng);
+    const size_t nchunks = bounds.size() - 1;
     if (nchunks <= 1) {
         HostProgram hp;
         qsim::compile(c->n, c->dtype, c->cfg, g, ng, mats, nm, hp);
@@ -910,7 +920,7 @@ qsim_status compile_chunks(qsim_ctx *c, const qsim_gate *g, size_t ng, const dou
                 if (stop || next.load() >= nchunks) return;
                 i = next++;
             }
-            const size_t b = i * C, e = std::min(ng, b + C);
+            const size_t b = bounds[i], e = bounds[i + 1];
             HostProgram hp;
             qsim::compile(c->n, c->dtype, c->cfg, g + b, e - b, mats, nm, hp);
             auto pk = std::make_unique<Packed>();

@@ -213,8 +213,13 @@ QSIM_API qsim_status qsim_apply(qsim_ctx *ctx, const qsim_gate *gates, size_t n_
  * The program belongs to the context that compiled it (same n and dtype). */
 QSIM_API qsim_status qsim_compile(qsim_ctx *ctx, const qsim_gate *gates, size_t n_gates,
                          const double *mats, size_t n_mats, qsim_program **out);
+/* Enqueue the program on the context's stream (asynchronous).  The first run
+ * with graphs != 2 in the config may capture the program's runs of tile passes
+ * as CUDA graphs on the host before enqueueing (see qsim_config.graphs). */
 QSIM_API qsim_status qsim_run(qsim_ctx *ctx, const qsim_program *prog);
 QSIM_API qsim_status qsim_program_get_info(const qsim_program *prog, qsim_program_info *info);
+/* Releases the program's device memory (stream-ordered) and host memory; a
+ * program holding CUDA graphs first synchronises the context's stream. */
 QSIM_API qsim_status qsim_program_free(qsim_program *prog);
 
 /* ------------------------------------------------------------ measurement --

@@ -250,9 +250,6 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                         const uint32_t j = H < 0 ? (uint32_t)q : (((uint32_t)q >> H) << (H + 1)) | ((uint32_t)q & ((1u << H) - 1));
                         u[q] = (__builtin_popcount(j & zr) & 1) ? -t : t;
                     }
-                    bool uniform = xr && !(xr & (xr - 1));
-                    for (int q = 1; q < cnt && uniform; q++) uniform = u[q] == u[0];
-                    if (uniform) r.sel |= 0x40;
                     for (int q = 0; q < cnt; q++) tab.push_back(u[q]);
                     for (int q = 0; q < cnt; q++) tab.push_back(-u[q]);
                     std::memcpy(&d, &r, sizeof(d));

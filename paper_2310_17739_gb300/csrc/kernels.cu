@@ -534,37 +534,6 @@ __device__ __forceinline__ void rot_reg_dispatch(float2 *a, unsigned sel, const 
     }
 }
 
-// A one-bit X mask whose pairs all share the coefficient u.
-template <int XR, bool ODD>
-__device__ __forceinline__ void rot_reg_uniform(float2 *a, float u) {
-    constexpr int H = top_bit(XR);
-#pragma unroll
-    for (int p = 0; p < 16; p++) {
-        const int j = pair_lo(p, H);
-        const int k = j ^ XR;
-        const float2 aj = a[j], ak = a[k];
-        if (ODD) {
-            a[j] = make_float2(fmaf(-u, ak.y, aj.x), fmaf(u, ak.x, aj.y));
-            a[k] = make_float2(fmaf(-u, aj.y, ak.x), fmaf(u, aj.x, ak.y));
-        } else {
-            a[j] = make_float2(fmaf(-u, ak.x, aj.x), fmaf(-u, ak.y, aj.y));
-            a[k] = make_float2(fmaf(u, aj.x, ak.x), fmaf(u, aj.y, ak.y));
-        }
-    }
-}
-
-// sel & 63 = xr << 1 | odd with xr one slot bit.
-__device__ __forceinline__ void rot_uniform_dispatch(float2 *a, unsigned sel, float u) {
-    switch (sel & 63u) {
-#define QSIM_U(v)                                        \
-    case 2 * v: rot_reg_uniform<v, false>(a, u); break;  \
-    case 2 * v + 1: rot_reg_uniform<v, true>(a, u); break;
-        QSIM_U(1) QSIM_U(2) QSIM_U(4) QSIM_U(8) QSIM_U(16)
-#undef QSIM_U
-        default: break;
-    }
-}
-
 // The rotations of one segment, on this thread's registers: each takes the
 // half of its coefficient table that matches the thread's Z parity (RegRot).
 __device__ __forceinline__ void seg_rotations(float2 *reg, const RegRot *ops, uint32_t count, uint32_t tb,
@@ -572,9 +541,7 @@ __device__ __forceinline__ void seg_rotations(float2 *reg, const RegRot *ops, ui
     for (uint32_t k = 0; k < count; k++) {
         const RegRot op = ops[k];
         const uint32_t pt = (__popc(tb & op.zt) ^ __popc(op.zc & bid)) & 1u;
-        if (op.sel & 0x40u) {
-            rot_uniform_dispatch(reg, op.sel, coef[op.tab + 16 * pt]);
-        } else if (op.sel >> 1) {
+        if (op.sel >> 1) {
             rot_reg_dispatch(reg, op.sel, reinterpret_cast<const float4 *>(coef + op.tab + 16 * pt));
         } else {
             rot_reg_diag(reg, reinterpret_cast<const float4 *>(coef + op.tab + 32 * pt), op.sel & 1u);

@@ -140,9 +140,7 @@ cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const ui
 // in registers, flags = number of rotations that follow in the segment.
 constexpr uint8_t kSegMarker = 8;
 // A rotation inside a register segment (the 16 bytes of a DevOp slot).  sel =
-// uniform << 6 | xr << 1 | odd, xr its X mask over the segment's 5 register
-// slots, uniform set when xr is one slot bit and its 16 coefficients are equal
-// (the kernel then reads only the first of its half); zt its
+// xr << 1 | odd, xr its X mask over the segment's 5 register slots; zt its
 // tile-local Z mask; zc as in DevOp; tab = offset (in floats, a multiple of
 // 4) of its coefficient table in the pass's coefficient slice.  The table
 // lists u_p = t (-1)^{parity(j_p & zr)}, t = W / cos theta, zr the Z mask over

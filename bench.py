@@ -419,8 +419,7 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     b = qs.Batch([c.n for c in cs], "c64", stream=stream, config=cfg, seeds=[0] * len(cs))
     t0 = time.perf_counter()
-    for i, c in enumerate(cs):
-        b.compile(i, c.gates)
+    b.compile_many([c.gates for c in cs])
     t_compile = time.perf_counter() - t0
 
     def step():
@@ -468,8 +467,7 @@ def run_batched(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for i, c in enumerate(cs):
-            b.compile(i, c.gates)
+        b.compile_many([c.gates for c in cs])
         step()
     torch.cuda.synchronize()
     dt_e2e = time.perf_counter() - t0

@@ -327,6 +327,16 @@ QSIM_API qsim_status qsim_batch_set_seeds(qsim_batch *b, const uint64_t *seeds);
  * replacing any earlier one.  Synchronous on the host compile only. */
 QSIM_API qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *gates,
                                         size_t n_gates, const double *mats, size_t n_mats);
+/* qsim_batch_compile for `count` instances at once: instance indices[k] gets
+ * gates[k][0, n_gates[k]) (mats NULL, or mats[k] / n_mats[k] as in
+ * qsim_batch_compile).  Every record is validated first (nothing changes on an
+ * invalid one); the host compiles the programs on `threads` threads (0 =
+ * auto), then uploads them in order, so the result equals count calls of
+ * qsim_batch_compile.  The caller's arrays may be freed after the call. */
+QSIM_API qsim_status qsim_batch_compile_many(qsim_batch *b, int count, const int32_t *indices,
+                                             const qsim_gate *const *gates, const size_t *n_gates,
+                                             const double *const *mats, const size_t *n_mats,
+                                             int threads);
 QSIM_API qsim_status qsim_batch_run(qsim_batch *b);
 /* Expectation values for every instance: instance i uses terms
  * [term_offsets[i], term_offsets[i+1]) and writes out[t] = coef_t * Re <psi_i|P_t|psi_i>

@@ -1689,6 +1689,66 @@ qsim_status qsim_batch_compile(qsim_batch *b, int index, const qsim_gate *g, siz
     return QSIM_OK;
 }
 
+qsim_status qsim_batch_compile_many(qsim_batch *b, int count, const int32_t *indices,
+                                    const qsim_gate *const *gates, const size_t *n_gates,
+                                    const double *const *mats, const size_t *n_mats, int threads) {
+    if (!b || count < 0) return bfail(b, QSIM_E_INVAL, "bad batch or count");
+    if (count && (!indices || !gates || !n_gates)) return bfail(b, QSIM_E_INVAL, "null argument");
+    for (int k = 0; k < count; k++) {
+        const int i = indices[k];
+        if (i < 0 || i >= b->count) return bfail(b, QSIM_E_INVAL, "bad batch index");
+        if (n_gates[k] && !gates[k]) return bfail(b, QSIM_E_INVAL, "gates is NULL");
+        std::string err;
+        if (!qsim::validate(b->inst[i]->n, gates[k], n_gates[k], mats ? mats[k] : nullptr, n_mats ? n_mats[k] : 0,
+                            err))
+            return bfail(b, QSIM_E_INVAL, err);
+    }
+    // host compilation of every program on worker threads (the same chunks as
+    // qsim_batch_compile), then the uploads in order on the batch stream
+    std::vector<std::vector<Packed>> packed((size_t)count);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int k = next++; k < count; k = next++) {
+            const int i = indices[k];
+            qsim_ctx *c = b->inst[i];
+            const double *mk = mats ? mats[k] : nullptr;
+            const size_t nmk = n_mats ? n_mats[k] : 0;
+            std::vector<size_t> bounds;
+            if (!b->resident[i]) bounds = chunk_bounds(c, n_gates[k]);
+            if (bounds.size() <= 2) bounds = {0, n_gates[k]};  // one program, as compile_chunks
+            for (size_t j = 0; j + 1 < bounds.size(); j++) {
+                const size_t lo = bounds[j], hi = bounds[j + 1];
+                HostProgram hp;
+                qsim::compile(c->n, c->dtype, c->cfg, gates[k] + lo, hi - lo, mk, nmk, hp);
+                packed[k].emplace_back();
+                pack(hp, c->dtype, b->resident[i] ? false : allow_reg(c), packed[k].back());
+            }
+        }
+    };
+    const int T = std::max(1, std::min(threads > 0 ? threads : compile_threads(b->aux), count));
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; t++) th.emplace_back(worker);
+    worker();
+    for (auto &t : th) t.join();
+    b->drop_graph();
+    for (int k = 0; k < count; k++) {
+        const int i = indices[k];
+        release_instance_program(b, i);
+        for (const Packed &pk : packed[k]) {
+            DevChunk dc;
+            qsim_status st = upload_chunk(b->aux, pk, dc);
+            if (st != QSIM_OK) {
+                release_chunk(b->aux, dc);
+                release_instance_program(b, i);
+                return bfail(b, st, b->aux->err);
+            }
+            b->prog[i].push_back(std::move(dc));
+        }
+        std::vector<Packed>().swap(packed[k]);
+    }
+    return QSIM_OK;
+}
+
 }  // extern "C"
 
 namespace {

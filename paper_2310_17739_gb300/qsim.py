@@ -83,6 +83,7 @@ _SIGS = {
     "qsim_batch_set_config": ([_vp, ctypes.POINTER(QsimConfig)], _i32),
     "qsim_batch_set_seeds": ([_vp, _vp], _i32),
     "qsim_batch_compile": ([_vp, _i32, _vp, _sz, _vp, _sz], _i32),
+    "qsim_batch_compile_many": ([_vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
     "qsim_batch_run": ([_vp], _i32),
     "qsim_batch_expect": ([_vp, _vp, _vp, _vp], _i32),
     "qsim_batch_state": ([_vp, _i32, _vp, _sz, _i32], _i32),
@@ -393,6 +394,21 @@ class Batch:
         g = _gates(gates)
         m = _mats(mats)
         _check(_lib.qsim_batch_compile(self.h, index, _ptr(g), g.size, _ptr(m), m.size))
+
+    def compile_many(self, gate_lists, indices=None, mats_lists=None, threads: int = 0):
+        """compile(i, gates) for many instances at once (host compilation on
+        worker threads); indices default to 0..len(gate_lists)-1."""
+        idx = np.arange(len(gate_lists), dtype=np.int32) if indices is None else \
+            np.ascontiguousarray(indices, dtype=np.int32)
+        gs = [_gates(g) for g in gate_lists]
+        ms = [_mats(m) for m in (mats_lists or [None] * len(gs))]
+        k = len(gs)
+        gp = (ctypes.c_void_p * max(k, 1))(*[g.ctypes.data if g.size else None for g in gs])
+        ng = np.array([g.size for g in gs], dtype=np.uint64)
+        mp = (ctypes.c_void_p * max(k, 1))(*[m.ctypes.data if m.size else None for m in ms])
+        nm = np.array([m.size for m in ms], dtype=np.uint64)
+        _check(_lib.qsim_batch_compile_many(self.h, k, _ptr(idx), ctypes.cast(gp, ctypes.c_void_p), _ptr(ng),
+                                            ctypes.cast(mp, ctypes.c_void_p), _ptr(nm), threads))
 
     def run(self):
         _check(_lib.qsim_batch_run(self.h))

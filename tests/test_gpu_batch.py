@@ -119,3 +119,25 @@ def test_batch_argument_errors():
     with pytest.raises(qs.QsimError):
         b.expect([W.z_terms(4), W.z_terms(4)])   # instance 0 has 3 qubits
     b.close()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_compile_many_equals_one_by_one(dtype):
+    """qsim_batch_compile_many (host compilation on worker threads) gives the
+    same programs as qsim_batch_compile per instance: bitwise-equal states and
+    outcomes, indices in any order, and an invalid record rejects the call."""
+    cs = mixed_circuits(seed=70)
+    seeds = [3 + i for i in range(len(cs))]
+    cfg = dict(fusion=2)
+    ref = run_batch(cs, dtype, cfg, seeds)
+    b = qs.Batch([c.n for c in cs], dtype, config=cfg, seeds=seeds)
+    order = list(reversed(range(len(cs))))
+    b.compile_many([cs[i].gates for i in order], indices=order, mats_lists=[cs[i].mats for i in order],
+                   threads=4)
+    b.run()
+    for i in range(len(cs)):
+        assert np.array_equal(b.state(i), ref.state(i))
+    bad = cs[0].gates.copy()
+    bad["q0"][0] = 99
+    with pytest.raises(qs.QsimError):
+        b.compile_many([cs[1].gates, bad], indices=[1, 0])

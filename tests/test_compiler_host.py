@@ -293,17 +293,37 @@ def test_invalid_records_rejected_on_host():
 
 
 # ----------------------------------------------- Pauli-gadget recognition ----
+def pauli_times_by_index(psi, n, x, z):
+    """P psi by permuting indices: P|j> = i^popcount(x & z) (-1)^popcount(j & z) |j ^ x>
+    (pinned to the Kronecker form in test_pauli_times_by_index_equals_kronecker)."""
+    j = np.arange(1 << n, dtype=np.int64)
+    par = np.zeros(1 << n, dtype=np.int64)
+    zz = j & z
+    while np.any(zz):
+        par ^= zz & 1
+        zz >>= 1
+    out = np.empty_like(psi)
+    out[j ^ x] = (1j) ** (bin(x & z).count("1") % 4) * np.where(par, -1.0, 1.0) * psi
+    return out
+
+
+def pauli_times(psi, n, x, z):
+    """P psi: a dense Kronecker product up to 10 qubits, by index above."""
+    if n <= 10:
+        return H.term_dense(n, x, z) @ psi
+    return pauli_times_by_index(psi, n, x, z)
+
+
 def apply_compiled(psi, n, ops):
     """Apply a compiled op list with numpy: dense blocks by reshaping, Pauli
-    rotations as cos(t) I - i sin(t) P with P a dense Kronecker product."""
+    rotations as cos(t) I - i sin(t) P."""
     for o in ops:
         if o[0] == "pauli":
             _, x, z, t = o
-            P = H.term_dense(n, x, z)
-            psi = np.cos(t) * psi - 1j * np.sin(t) * (P @ psi)
+            psi = np.cos(t) * psi - 1j * np.sin(t) * pauli_times(psi, n, x, z)
         elif o[0] == "frame":  # i^g exp(-i pi/2 P) = i^g (-i) P
             _, x, z, g = o
-            psi = (1j) ** g * (-1j) * (H.term_dense(n, x, z) @ psi)
+            psi = (1j) ** g * (-1j) * pauli_times(psi, n, x, z)
         elif o[0] == "event":
             raise AssertionError("events are not applied here")
         else:
@@ -398,12 +418,22 @@ def test_near_miss_blocks_stay_gates():
         assert np.abs(apply_compiled(psi, n, ops) - ref).max() < 1e-12
 
 
-@pytest.mark.parametrize("tile_bits", [7, 9])
-def test_pauli_schedule_reordering_is_exact(tile_bits):
-    """Commuting rotations are pulled into earlier passes; the state still matches."""
-    n = 10
+def test_pauli_times_by_index_equals_kronecker():
+    rng = np.random.default_rng(5)
+    for n in (1, 3, 6):
+        for _ in range(20):
+            x, z = int(rng.integers(0, 1 << n)), int(rng.integers(0, 1 << n))
+            psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+            assert np.allclose(pauli_times_by_index(psi, n, x, z), H.term_dense(n, x, z) @ psi, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,tile_bits,dtype", [(10, 7, "c128"), (10, 9, "c128"), (15, 0, "c64"),
+                                                (16, 0, "c64")])
+def test_pauli_schedule_reordering_is_exact(n, tile_bits, dtype):
+    """Commuting rotations are pulled into earlier passes (also with the default
+    complex64 rotation tiles, 11 and 12 dimensions here); the state still matches."""
     c = W.ucc_circuit(n, seed=17, n_gadgets=60, w_lo=2, w_hi=6, target_gates=1500, n_meas=3)
-    ops = qs.fuse(n, c.gates, dtype=qs.C128, fusion=2, tile_bits=tile_bits)
+    ops = qs.fuse(n, c.gates, dtype=qs.C64 if dtype == "c64" else qs.C128, fusion=2, tile_bits=tile_bits)
     order = [i for i, o in enumerate(ops) if o[0] == "pauli"]
     assert len(order) == c.meta["n_gadgets_total"]
     recs, mats = [], []

@@ -34,6 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+# the large workload's metric and description, shared by both arms
+METRIC_LARGE = "gates/s at 21 qubits (UCC-style circuit)"
+WORKLOAD_LARGE = ("21-qubit UCC-style Trotter circuit (2,000 weight 2-6 Pauli exponentials per step, "
+                  "cycled) with 8 mid-circuit measurements")
 
 
 def parse():
@@ -186,12 +190,12 @@ def run_reference(args):
         oracle.run(psi, c.n, c.gates[:k])
     dt = time.perf_counter() - t0
     v = k * args.steps / dt
-    line = {"metric": "gates/s at 21 qubits (UCC-style circuit)", "value": v, "unit": "gates/s",
+    line = {"metric": METRIC_LARGE, "value": v, "unit": "gates/s",
             "impl": "reference", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"21-qubit UCC-style circuit, first {k} of {c.G} gates per step "
-                                   "(bounded CPU sample)", "n_qubits": 21},
+            "config": {"workload": WORKLOAD_LARGE, "n_qubits": 21, "gates": c.G,
+                       "sample": f"first {k} of {c.G} gates per step (bounded CPU sample)"},
             "cpu_baseline": {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {k} gates per step, complex128, unfused"},
             "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -366,14 +370,13 @@ def run_ours(args):
                 "includes": "FP64 prefix sums of the 2^21 Born weights, 1e6 Philox draws and searches, "
                             "read-back to host (qsim_sample)"}
     line = {
-        "metric": "gates/s at 21 qubits (UCC-style circuit, complex64)",
+        "metric": METRIC_LARGE,
         "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": "complex64 amplitudes, FP32 gate arithmetic, FP64 reductions/renormalisation",
         "data": "synthetic",
-        "config": {"workload": "21-qubit UCC-style Trotter circuit (2,000 weight 2-6 Pauli "
-                               "exponentials per step, cycled) with 8 mid-circuit measurements",
+        "config": {"workload": WORKLOAD_LARGE,
                    "n_qubits": 21, "gates": c.G, "measurements": info["measurements"],
                    "fused_ops": info["fused_ops"], "passes": info["passes"],
                    "fusion": {0: "none", 1: "paper stages 1-4",

@@ -152,3 +152,55 @@ def test_errors_name_the_line(text, where):
     with pytest.raises(qs.QsimError) as e:
         qs.parse_qasm(text)
     assert e.value.status == qs.E_INVAL and where in str(e.value)
+
+
+def test_expression_functions_numbers_and_precedence():
+    """Parameter expressions: unary functions, exponent notation, leading-dot
+    numbers, right-associative ^, unary minus binding tighter than ^ is NOT
+    assumed (-2^2 = -4, as in the OpenQASM 2.0 grammar's precedence)."""
+    text = """OPENQASM 2.0; qreg q[1];
+rz(sin(pi/6) + cos(0)) q[0];
+rz(sqrt(16) * exp(0) - ln(1)) q[0];
+rz(tan(pi/4)) q[0];
+rz(1e-3 + .5 + 2.5E1) q[0];
+rz(2^3^2) q[0];
+rz(-2^2) q[0];
+rz((1 - 3) * -2 / 4) q[0];
+"""
+    _, g, _ = qs.parse_qasm(text)
+    got = [float(r["p"][0]) for r in g]
+    want = [1.5, 4.0, 1.0, 25.501, 512.0, -4.0, 1.0]
+    assert np.allclose(got, want, rtol=0, atol=1e-12), got
+
+
+def test_builtin_u_cx_and_nested_user_gates():
+    """U and CX (the language's built-ins) and a user gate calling another one
+    with expressions of its parameters, against the oracle."""
+    text = """OPENQASM 2.0; qreg q[3];
+gate inner(a) x, y { U(a, 0, 0) x; CX x, y; }
+gate outer(b, c) x, y, z { inner(b / 2) x, y; inner(-c) y, z; rz(b + c) z; }
+outer(0.8, 0.3) q[0], q[1], q[2];
+"""
+    n, g, m = qs.parse_qasm(text)
+    assert n == 3
+    ops = [int(r["op"]) for r in g]
+    assert ops == [OP["U3"], OP["CX"], OP["U3"], OP["CX"], OP["RZ"]]
+    ref = W.records([(OP["U3"], 0, 0, 0.4, 0.0, 0.0, 0, 0), (OP["CX"], 0, 1, 0, 0, 0, 0, 0),
+                     (OP["U3"], 1, 0, -0.3, 0.0, 0.0, 0, 0), (OP["CX"], 1, 2, 0, 0, 0, 0, 0),
+                     (OP["RZ"], 2, 0, 1.1, 0.0, 0.0, 0, 0)])
+    psi = W.random_state(n, seed=4)
+    a, b = psi.copy(), psi.copy()
+    oracle.run(a, n, g, m)
+    oracle.run(b, n, ref)
+    assert np.abs(a - b).max() < 1e-13
+
+
+@pytest.mark.parametrize("text,where", [
+    ("OPENQASM 2.0; qreg a[2]; qreg b[3]; cx a, b;", "registers of different sizes"),
+    ("OPENQASM 2.0; qreg q[1]; opaque g q;", "'opaque' is not supported"),
+    ("OPENQASM 2.0; qreg q[1]; rz(foo) q[0];", "foo"),
+])
+def test_more_errors(text, where):
+    with pytest.raises(qs.QsimError) as e:
+        qs.parse_qasm(text)
+    assert e.value.status == qs.E_INVAL and where in str(e.value)

@@ -156,8 +156,8 @@ def test_errors_name_the_line(text, where):
 
 def test_expression_functions_numbers_and_precedence():
     """Parameter expressions: unary functions, exponent notation, leading-dot
-    numbers, right-associative ^, unary minus binding tighter than ^ is NOT
-    assumed (-2^2 = -4, as in the OpenQASM 2.0 grammar's precedence)."""
+    numbers, right-associative ^, and ^ binding tighter than unary minus
+    (-2^2 = -4)."""
     text = """OPENQASM 2.0; qreg q[1];
 rz(sin(pi/6) + cos(0)) q[0];
 rz(sqrt(16) * exp(0) - ln(1)) q[0];

@@ -142,6 +142,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest value of x over the ranks (a job's time is its slowest
+    rank's); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest rank's seconds."""
+    return units_per_rank * world / seconds
+
+
 def workload(gates):
     from paper_2310_17739_gb300 import workload as W
     return W.config_large(target_gates=gates, n_meas=8)
@@ -292,13 +310,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     out, probs = sim.outcomes()
-    value = c.G * args.steps * world / (ms / 1e3)
+    value = aggregate(c.G * args.steps, world, ms / 1e3)
     # side measurement: final-state shots of the end state (qsim_sample)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -319,13 +333,8 @@ def run_ours(args):
             z2 = sim2.expect(zt)
             o2, p2 = sim2.outcomes()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": c.G * args.steps * world / dt, "unit": "gates/s",
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": aggregate(c.G * args.steps, world, dt), "unit": "gates/s",
                "h2d_bytes_per_step": int(info["device_bytes"] + zt.nbytes),
                "d2h_bytes_per_step": int(zt.size * 8 + o2.nbytes + p2.nbytes + 64),
                "includes": "host fusion + scheduling (pipelined), program upload, kernels, read-back"}
@@ -458,13 +467,8 @@ def run_batched(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = len(cs) * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    value = aggregate(len(cs) * args.steps, world, ms / 1e3)
 
     # end to end from host gate records: compile + upload + run + <H> read-back
     barrier()

@@ -273,12 +273,13 @@ int conj_z(const cd *U, int *sgn) {
 bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double *mats, size_t nm,
                   Gadget &out) {
     (void)n;
-    const size_t kMaxLead = 16;
+    constexpr size_t kMaxLead = 16;
     size_t j = i;
     uint64_t lead_mask = 0;
-    std::vector<std::pair<uint32_t, size_t>> lead;  // (qubit, gate index)
-    while (j < end && lead.size() < kMaxLead && is_basis_gate(g[j])) {
-        lead.emplace_back(g[j].q0, j);
+    size_t lead[kMaxLead];  // gate indices of the leading 1-qubit gates
+    size_t nl = 0;
+    while (j < end && nl < kMaxLead && is_basis_gate(g[j])) {
+        lead[nl++] = j;
         lead_mask |= 1ull << g[j].q0;
         j++;
     }
@@ -298,20 +299,20 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
     }
     j += nf;
     // parity set: bits XORed into t by the network
-    uint64_t rowmask[64];
+    uint64_t rowmask[64];  // only the touched qubits' entries are read
     uint64_t touched = 1ull << t;
     for (size_t k = f0; k < f1; k++) touched |= (1ull << g[k].q0) | (1ull << g[k].q1);
-    for (int q = 0; q < 64; q++) rowmask[q] = (touched >> q) & 1 ? (1ull << q) : 0;
+    for (uint64_t r = touched; r; r &= r - 1) rowmask[__builtin_ctzll(r)] = r & -r;
     for (size_t k = f0; k < f1; k++) rowmask[g[k].q1] ^= rowmask[g[k].q0];
     const uint64_t S = rowmask[t];
     if (popc(S) < 2) return false;
     // per-qubit lead products
     cd Ulead[64][4];
     int nlead[64] = {0};
-    for (auto &pr : lead) {
-        const uint32_t q = pr.first;
+    for (size_t e0 = 0; e0 < nl; e0++) {
+        const uint32_t q = g[lead[e0]].q0;
         cd m[16];
-        if (gate_matrix(g[pr.second], mats, nm, m) != 2) return false;
+        if (gate_matrix(g[lead[e0]], mats, nm, m) != 2) return false;
         if (nlead[q] == 0) {
             for (int e = 0; e < 4; e++) Ulead[q][e] = m[e];
         } else {
@@ -325,7 +326,7 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
     // trailing: as many 1-qubit gates per qubit as the lead had, undoing it
     cd Utrail[64][4];
     int ntrail[64] = {0};
-    size_t need = lead.size();
+    size_t need = nl;
     while (need > 0) {
         if (j >= end || !is_basis_gate(g[j])) return false;
         const uint32_t q = g[j].q0;
@@ -347,7 +348,8 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
     // trail * lead == I on every basis-changed qubit, letters from U^dag Z U
     uint64_t xm = 0, zm = 0;
     int sign = 1;
-    for (int q = 0; q < 64; q++) {
+    for (uint64_t r = lead_mask | S; r; r &= r - 1) {
+        const int q = __builtin_ctzll(r);
         const bool inS = (S >> q) & 1;
         if (nlead[q]) {
             const cd *A = Utrail[q], *B = Ulead[q];

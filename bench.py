@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--k-max", type=int, default=2)
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
                     help="with --fusion >= 0: resident-block rotation passes")
+    ap.add_argument("--forced-low", type=int, default=0,
+                    help="with --fusion >= 0: low qubits kept in every tile (0: the library's default)")
     ap.add_argument("--fusion", type=int, default=-1,
                     help="-1: autotune (paper fusion, k-qubit merge, Pauli-gadget rotations); "
                          "0/1/2 force a fusion level")
@@ -272,6 +274,8 @@ def run_ours(args):
     else:
         cfg = dict(fusion=args.fusion, k_max=args.k_max, tile_bits=args.tile_bits or 13,
                    persistent=args.persistent)
+        if args.forced_low:
+            cfg["forced_low"] = args.forced_low
     stream = torch.cuda.current_stream()
     sim = qs.Sim(n, "c64", stream=stream, config=cfg, seed=1003)
     t0 = time.perf_counter()
@@ -361,7 +365,8 @@ def run_ours(args):
     # DRAM traffic of one launch from the ncu capture summarised in
     # profiles/rot_pass_21q_c64_m12.md (that exact configuration only)
     traffic, traffic_src = None, None
-    if cfg.get("fusion") == 2 and cfg.get("tile_bits") == 12 and not cfg.get("threads") and not cfg.get("persistent"):
+    if (cfg.get("fusion") == 2 and cfg.get("tile_bits") == 12 and not cfg.get("threads")
+            and not cfg.get("persistent") and not cfg.get("forced_low")):
         traffic = 16854528
         traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, m = 12 "
                        "(caches flushed before the launch: the state's cold read; writes stay in L2)")

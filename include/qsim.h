@@ -153,6 +153,12 @@ typedef struct {
  *          pass launched from the host).  Graphs are rebuilt after
  *          qsim_set_config; persistent = 1 never uses them.  The server
  *          launches its requests' passes from the host.
+ * forced_low  low qubits kept in every tile so that tile rows are contiguous
+ *          (0 = 4 for complex64, 3 for complex128: 128-byte rows; 1..8 any
+ *          other count, raised to m - 10 when below).  Fewer forced qubits
+ *          leave more tile dimensions for rotations (fewer passes) at the cost
+ *          of shorter contiguous rows.  Resident-block passes (persistent = 1)
+ *          need 4 and fall back to one block per tile below that.
  */
 typedef struct {
     int32_t fusion;
@@ -164,6 +170,7 @@ typedef struct {
     int32_t compile_threads;
     int32_t persistent;
     int32_t graphs;
+    int32_t forced_low;
 } qsim_config;
 
 typedef struct {

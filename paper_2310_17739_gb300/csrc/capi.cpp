@@ -661,8 +661,9 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
             c->prof_open = true;
             c->prof_in_window = 0;
         }
-        if (p.reg && c->cfg.persistent && dc.m <= 13) {
-            const uint64_t *basis = dc.bvec.data() + p.basis;
+        const uint64_t *pb = dc.bvec.data() + p.basis;
+        if (p.reg && c->cfg.persistent && dc.m <= 13 && pb[0] == 1 && pb[1] == 2 && pb[2] == 4 && pb[3] == 8) {
+            const uint64_t *basis = pb;
             if (!c->tile_ctr) {
                 c->tile_ctr = (unsigned long long *)dalloc(c, sizeof(unsigned long long));
                 if (!c->tile_ctr) return fail(c, QSIM_E_OOM, "tile counter allocation failed");
@@ -1088,6 +1089,7 @@ qsim_status qsim_set_config(qsim_ctx *c, const qsim_config *cfg) {
         return fail(c, QSIM_E_INVAL, "negative size");
     if (cfg->persistent != 0 && cfg->persistent != 1) return fail(c, QSIM_E_INVAL, "persistent must be 0 or 1");
     if (cfg->graphs < 0 || cfg->graphs > 2) return fail(c, QSIM_E_INVAL, "graphs must be 0, 1 or 2");
+    if (cfg->forced_low < 0 || cfg->forced_low > 8) return fail(c, QSIM_E_INVAL, "forced_low must be in [0, 8]");
     c->cfg = qsim::config_from(cfg);
     c->cfg_gen++;
     return QSIM_OK;

@@ -391,6 +391,7 @@ Config config_from(const qsim_config *c) {
     k.compile_threads = c->compile_threads;
     k.persistent = c->persistent;
     k.graphs = c->graphs;
+    k.forced_low = c->forced_low;
     return k;
 }
 
@@ -405,6 +406,7 @@ void config_to(const Config &c, qsim_config *o) {
     o->compile_threads = c.compile_threads;
     o->persistent = c.persistent;
     o->graphs = c.graphs;
+    o->forced_low = c.forced_low;
 }
 
 static int max_tile_bits(qsim_dtype dt) { return dt == QSIM_C64 ? 14 : 13; }
@@ -429,8 +431,9 @@ int tile_bits_for(const Config &cfg, int n, qsim_dtype dtype) {
     return std::max(m, 1);
 }
 
-int forced_low_bits(qsim_dtype dtype, int m) {
-    int L = dtype == QSIM_C64 ? 4 : 3;  // 16 x 8 B or 8 x 16 B = 128-byte runs
+int forced_low_bits(qsim_dtype dtype, int m, int requested) {
+    int L = requested > 0 ? requested : (dtype == QSIM_C64 ? 4 : 3);  // 16 x 8 B or 8 x 16 B
+    L = std::max(L, m - 10);
     return std::min(L, m);
 }
 
@@ -702,7 +705,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
 
     out.m = m;
     out.resident = (m == n);
-    const int L = forced_low_bits(dtype, m);
+    const int L = forced_low_bits(dtype, m, cfg.forced_low);
     const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
     const size_t W = cfg.lookahead > 0 ? (size_t)cfg.lookahead : 64;
     const bool reg_candidate = dtype == QSIM_C64 && !out.resident && m >= 10 && m <= 14;

@@ -152,6 +152,7 @@ struct Config {
     int compile_threads = 0;
     int persistent = 0;
     int graphs = 0;
+    int forced_low = 0;
 };
 
 Config config_from(const qsim_config *c);
@@ -159,8 +160,11 @@ void config_to(const Config &c, qsim_config *out);
 
 // Tile size (qubits) used for an n-qubit state of this dtype.
 int tile_bits_for(const Config &cfg, int n, qsim_dtype dtype);
-// Qubits always kept in every tile so that tile rows are 128-byte runs.
-int forced_low_bits(qsim_dtype dtype, int m);
+// Qubits always kept in every tile so that tile rows are contiguous runs
+// (default 128 bytes: 4 for complex64, 3 for complex128; `requested` > 0
+// overrides), never fewer than m - 10 (the generic pass tabulates at most
+// 1,024 row offsets).
+int forced_low_bits(qsim_dtype dtype, int m, int requested = 0);
 
 // Compiled host program: fused ops (with FP64 matrices) in execution order and
 // the pass schedule over them.

@@ -36,7 +36,7 @@ class QsimConfig(ctypes.Structure):
     _fields_ = [("fusion", ctypes.c_int32), ("k_max", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("chunk_gates", ctypes.c_int32),
                 ("lookahead", ctypes.c_int32), ("compile_threads", ctypes.c_int32),
-                ("persistent", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("graphs", ctypes.c_int32), ("forced_low", ctypes.c_int32)]
 
 
 class ProgramInfo(ctypes.Structure):
@@ -147,9 +147,9 @@ def _mats(m):
 
 
 def make_config(fusion=1, k_max=2, tile_bits=0, threads=0, chunk_gates=0, lookahead=0,
-                compile_threads=0, persistent=0, graphs=0) -> QsimConfig:
+                compile_threads=0, persistent=0, graphs=0, forced_low=0) -> QsimConfig:
     return QsimConfig(fusion, k_max, tile_bits, threads, chunk_gates, lookahead, compile_threads, persistent,
-                      graphs)
+                      graphs, forced_low)
 
 
 # ----------------------------------------------------------- torch plumbing --
@@ -238,7 +238,7 @@ class Sim:
         _check(_lib.qsim_get_config(self.h, ctypes.byref(c)), self.h)
         return dict(fusion=c.fusion, k_max=c.k_max, tile_bits=c.tile_bits, threads=c.threads,
                     chunk_gates=c.chunk_gates, lookahead=c.lookahead, compile_threads=c.compile_threads,
-                    persistent=c.persistent, graphs=c.graphs)
+                    persistent=c.persistent, graphs=c.graphs, forced_low=c.forced_low)
 
     def set_seed(self, seed: int):
         _check(_lib.qsim_set_seed(self.h, seed), self.h)

@@ -185,16 +185,22 @@ def _span_contains(basis, v):
     return v == 0
 
 
-@pytest.mark.parametrize("dtype,tile_bits,fusion", [(0, 0, 2), (0, 10, 2), (1, 9, 2), (0, 9, 1)])
-def test_subspace_schedule_invariants(dtype, tile_bits, fusion):
+@pytest.mark.parametrize("dtype,tile_bits,fusion,forced_low", [(0, 0, 2, 0), (0, 10, 2, 0), (1, 9, 2, 0),
+                                                              (0, 9, 1, 0), (0, 12, 2, 3), (0, 12, 2, 2),
+                                                              (0, 13, 1, 2)])
+def test_subspace_schedule_invariants(dtype, tile_bits, fusion, forced_low):
     """Every pass's tile is an m-dimensional subspace that holds each dense
     op's qubit unit vectors and each rotation's X mask; the forced low qubits
-    lead the basis; the pivots are m distinct positions."""
+    lead the basis (4 / 3 by dtype, or forced_low, never fewer than m - 10);
+    the pivots are m distinct positions."""
     n = 16
     c = W.ucc_circuit(n, seed=11, n_gadgets=120, w_lo=2, w_hi=8, target_gates=8000, n_meas=4)
-    ops = qs.fuse(n, c.gates, dtype=dtype, fusion=fusion, tile_bits=tile_bits)
-    passes = qs.schedule(n, c.gates, dtype=dtype, fusion=fusion, tile_bits=tile_bits, with_basis=True)
-    L = 4 if dtype == 0 else 3
+    ops = qs.fuse(n, c.gates, dtype=dtype, fusion=fusion, tile_bits=tile_bits, forced_low=forced_low)
+    passes = qs.schedule(n, c.gates, dtype=dtype, fusion=fusion, tile_bits=tile_bits, with_basis=True,
+                         forced_low=forced_low)
+    L = forced_low or (4 if dtype == 0 else 3)
+    if tile_bits:
+        L = max(L, tile_bits - 10)
     covered = 0
     for tile, first, count, basis in passes:
         assert first == covered
@@ -214,6 +220,16 @@ def test_subspace_schedule_invariants(dtype, tile_bits, fusion):
         if fusion == 1:
             assert sorted(basis) == [1 << b for b in range(n) if (tile >> b) & 1]
     assert covered == len(ops)
+
+
+def test_fewer_forced_low_qubits_give_fewer_passes():
+    """Each forced low qubit takes a tile dimension from the rotations: with 3
+    or 2 instead of 4 the 21-qubit rotation stream needs fewer passes."""
+    n = 21
+    c = W.ucc_circuit(n, seed=3, n_gadgets=2000, w_lo=2, w_hi=6, target_gates=60000)
+    counts = [len(qs.schedule(n, c.gates, dtype=qs.C64, fusion=2, tile_bits=12, forced_low=L)) for L in (4, 3, 2)]
+    assert counts[0] == len(qs.schedule(n, c.gates, dtype=qs.C64, fusion=2, tile_bits=12))
+    assert counts[0] > counts[1] > counts[2]
 
 
 def test_subspace_tiles_hold_more_rotations_per_pass():
@@ -427,13 +443,16 @@ def test_pauli_times_by_index_equals_kronecker():
             assert np.allclose(pauli_times_by_index(psi, n, x, z), H.term_dense(n, x, z) @ psi, atol=1e-13)
 
 
-@pytest.mark.parametrize("n,tile_bits,dtype", [(10, 7, "c128"), (10, 9, "c128"), (15, 0, "c64"),
-                                                (16, 0, "c64")])
-def test_pauli_schedule_reordering_is_exact(n, tile_bits, dtype):
+@pytest.mark.parametrize("n,tile_bits,dtype,forced_low", [(10, 7, "c128", 0), (10, 9, "c128", 0),
+                                                           (15, 0, "c64", 0), (16, 0, "c64", 0),
+                                                           (16, 12, "c64", 2)])
+def test_pauli_schedule_reordering_is_exact(n, tile_bits, dtype, forced_low):
     """Commuting rotations are pulled into earlier passes (also with the default
-    complex64 rotation tiles, 11 and 12 dimensions here); the state still matches."""
+    complex64 rotation tiles, 11 and 12 dimensions here, and with 2 forced low
+    qubits); the state still matches."""
     c = W.ucc_circuit(n, seed=17, n_gadgets=60, w_lo=2, w_hi=6, target_gates=1500, n_meas=3)
-    ops = qs.fuse(n, c.gates, dtype=qs.C64 if dtype == "c64" else qs.C128, fusion=2, tile_bits=tile_bits)
+    ops = qs.fuse(n, c.gates, dtype=qs.C64 if dtype == "c64" else qs.C128, fusion=2, tile_bits=tile_bits,
+                  forced_low=forced_low)
     order = [i for i, o in enumerate(ops) if o[0] == "pauli"]
     assert len(order) == c.meta["n_gadgets_total"]
     recs, mats = [], []

@@ -36,6 +36,13 @@ def expm(a):
     return scipy.linalg.expm(a)
 
 
+def _np_draw(seed, k):
+    """u(seed, k) from numpy.random.Philox alone (the block at counter k is
+    numpy's first block when started at counter k - 1)."""
+    bg = np.random.Philox(key=np.array([seed, 0], dtype=np.uint64), counter=(k - 1) % (1 << 256))
+    return (int(bg.random_raw(1)[0]) >> 11) * 2.0**-53
+
+
 # ------------------------------------------------------------ gate table ----
 @pytest.mark.parametrize("theta", [0.0, 0.3, -1.7, 2.9])
 def test_rotations_match_expm(theta):
@@ -285,6 +292,64 @@ def test_reset_moves_one_half():
     bits = (np.arange(1 << n) >> 1) & 1
     assert st == 0 and np.all(psi[bits == 1] == 0)
     assert abs(np.linalg.norm(psi) - 1) < 1e-14
+
+
+def _reset_one_expected(before, n, q):
+    """RESET with outcome 1, written out with numpy: amplitude i (bit q set)
+    lands on i with bit q cleared, scaled by 1/sqrt(p1) with p1 the raw (not
+    normalised) weight of the |1> half; the |1> half becomes zero."""
+    idx = np.arange(1 << n)
+    one = ((idx >> q) & 1) == 1
+    p1 = float(np.sum(np.abs(before[one]) ** 2))
+    want = np.zeros_like(before)
+    want[idx[one] & ~(1 << q)] = before[one] / math.sqrt(p1)
+    return want
+
+
+@pytest.mark.parametrize("q", [0, 1, 3])
+def test_reset_outcome_one_forced_by_zero_p0(q):
+    """p0 = 0 on qubit q makes the draw give 1 for every u in [0, 1) (strict
+    u < P0), so the move branch must run.  The state is left unnormalised
+    (norm^2 = 0.37) so that a missing or wrong 1/sqrt(p1) scale shows."""
+    n = 4
+    psi = W.random_state(n, seed=40 + q)
+    one = ((np.arange(1 << n) >> q) & 1) == 1
+    psi[~one] = 0
+    psi *= math.sqrt(0.37) / np.linalg.norm(psi)
+    before = psi.copy()
+    st, out, pr = oracle.reset(psi, n, q, seed=8, k=3)
+    assert (st, out) == (0, 1) and abs(pr - 1.0) < 1e-15
+    want = _reset_one_expected(before, n, q)
+    assert np.allclose(psi, want, rtol=1e-14, atol=1e-17)
+    assert np.all(psi[one] == 0)
+    assert abs(np.linalg.norm(psi) - 1) < 1e-14
+
+
+def test_reset_outcome_one_drawn_on_a_generic_state():
+    """Both halves populated; the (seed, k) pair is chosen with numpy's Philox
+    (independent of the oracle's) so that u >= P0, i.e. the draw gives 1."""
+    n, q = 5, 2
+    psi = W.random_state(n, seed=9)
+    psi *= math.sqrt(0.61) / np.linalg.norm(psi)
+    one = ((np.arange(1 << n) >> q) & 1) == 1
+    P0 = float(np.sum(np.abs(psi[~one]) ** 2) / np.sum(np.abs(psi) ** 2))
+    seed = 21
+    k = next(k for k in range(1000) if _np_draw(seed, k) >= P0 + 1e-9)
+    before = psi.copy()
+    st, out, pr = oracle.reset(psi, n, q, seed=seed, k=k)
+    assert (st, out) == (0, 1)
+    assert abs(pr - (1 - P0)) < 1e-14
+    want = _reset_one_expected(before, n, q)
+    assert np.allclose(psi, want, rtol=1e-14, atol=1e-17)
+    assert np.all(psi[one] == 0)
+    # and a (seed, k) pair whose draw gives 0 leaves the kept half in place
+    k0 = next(k for k in range(1000) if _np_draw(seed, k) < P0 - 1e-9)
+    psi0 = before.copy()
+    st, out, pr = oracle.reset(psi0, n, q, seed=seed, k=k0)
+    assert (st, out) == (0, 0)
+    p0 = float(np.sum(np.abs(before[~one]) ** 2))
+    assert np.allclose(psi0[~one], before[~one] / math.sqrt(p0), rtol=1e-14, atol=1e-17)
+    assert np.all(psi0[one] == 0)
 
 
 def test_born_statistics_chi2():

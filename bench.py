@@ -30,10 +30,19 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+# DRAM bytes (read + write) of one k_rot_pass launch of the 21-qubit circuit in
+# the configuration below, from one ncu capture of the current kernel (ncu
+# empties the caches before a replayed launch, so this is the state's cold
+# read; in the timed loop the state stays in L2); None: no capture yet.
+TRAFFIC_CONFIG = dict(fusion=2, k_max=2, tile_bits=12)
+TRAFFIC_PER_LAUNCH = None
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, k_rot_pass, 21 qubits, tile 12"
 # the large workload's metric and description, shared by both arms
 METRIC_LARGE = "gates/s at 21 qubits (UCC-style circuit)"
 WORKLOAD_LARGE = ("21-qubit UCC-style Trotter circuit (2,000 weight 2-6 Pauli exponentials per step, "
@@ -50,6 +59,9 @@ def parse():
                     help="gate count of the circuit (the named workload is 115,000,000)")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--k-max", type=int, default=2)
+    ap.add_argument("--threads", type=int, default=0, choices=[0, 256, 512],
+                    help="with --fusion >= 0: threads per block of the generic tile pass (256 / 512 also "
+                         "keep dense passes out of register segments)")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
                     help="with --fusion >= 0: resident-block rotation passes")
     ap.add_argument("--forced-low", type=int, default=0,
@@ -67,7 +79,14 @@ def parse():
                     help="large: 21-qubit 1.15e8-gate circuit (default); batched: 512 parameter "
                          "sets of a 12-qubit circuit + 256 circuits of width 10-18; serving: "
                          "Poisson arrivals of 10-22-qubit requests")
-    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="--workload serving: length of the arrival window")
+    ap.add_argument("--summary-serve-seconds", type=float, default=15.0,
+                    help="default workload: arrival window of the nested serving summary")
+    ap.add_argument("--no-summaries", action="store_true",
+                    help="default workload: skip the nested batched / serving summaries and the side measurements")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="steps of the end-to-end measurement (at most --steps)")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=24)
     ap.add_argument("--pool", type=int, default=96)
@@ -251,9 +270,108 @@ def l2_copy_gbs(torch, n):
     return 2 * src.numel() * 4 / best / 1e9
 
 
+def fp64_peak_tflops(torch):
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul, 4096^3, 2 N^3
+    flops), best of 5 (GB300's FP64 is a small fraction of its FP32 rate, so
+    complex128 gate arithmetic is FP64-bound)."""
+    N = 4096
+    a = torch.randn(N, N, dtype=torch.float64, device="cuda")
+    b = torch.randn(N, N, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    return 2 * N ** 3 / best / 1e12
+
+
+def pass_timing(sim, prog, reps=2):
+    """Run a compiled program `reps` times with every tile-pass launch inside a
+    CUDA-event window on the context stream; (ms per step, per-launch ms,
+    algorithmic bytes and flops per launch, launches)."""
+    import torch
+    sim.reset()
+    sim.run(prog)
+    sim.sync()
+    sim.profile_start(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    for _ in range(reps):
+        sim.reset()
+        sim.run(prog)
+    e1.record(sim.stream)
+    assert sim.sync() == 0
+    torch.cuda.synchronize()
+    pr = sim.profile_read()
+    sim.profile_start(0)
+    k = max(pr["samples"], 1)
+    return e0.elapsed_time(e1) / reps, pr["ms"] / k, pr["bytes"] / k, pr["flops"] / k, pr["launches"]
+
+
+def hbm_side(torch, cfg, hbm_peak, src, gates=300_000):
+    """The same recipe (2,000 weight 2-6 gadgets per Trotter step, cycled) at 26
+    qubits: a 512 MiB complex64 state, larger than L2, so every pass streams
+    the state through HBM; in the benchmark's configuration."""
+    from paper_2310_17739_gb300 import qsim as qs
+    from paper_2310_17739_gb300 import workload as W
+    n = 26
+    c = W.ucc_circuit(n, seed=3, n_gadgets=2000, w_lo=2, w_hi=6, theta="uniform", target_gates=gates)
+    sim = qs.Sim(n, "c64", config=cfg)
+    prog = sim.compile(c.gates)
+    step_ms, launch_ms, b, f, launches = pass_timing(sim, prog)
+    prog.free()
+    sim.close()
+    gbs = b / (launch_ms / 1e3) / 1e9
+    return {"workload": f"26 qubits (complex64, 512 MiB state), {c.G} gates of the same recipe",
+            "gates_per_s": c.G / (step_ms / 1e3), "passes": launches // 2, "avg_launch_ms": launch_ms,
+            "algorithmic_bytes_per_launch": b, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+            "frac": gbs / hbm_peak, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+            "timing": "CUDA events around every tile-pass launch window on the context stream"}
+
+
+def precision_check(torch, c, cfg, gates=8_000_000):
+    """The paper's arithmetic (complex128, FP64) against the benchmark's complex64
+    on a prefix of the benchmark circuit: complex128 throughput (fusion 2, tile
+    passes), its FP64 rate against a measured DGEMM peak, and the complex64
+    state's infidelity against the complex128 one."""
+    from paper_2310_17739_gb300 import qsim as qs
+    g = c.gates[:gates]
+    out = {"gates": int(len(g))}
+    states = {}
+    for dt, conf in (("c128", dict(fusion=2)), ("c64", cfg)):
+        sim = qs.Sim(c.n, dt, config=conf, seed=1003)
+        prog = sim.compile(g)
+        step_ms, launch_ms, b, f, launches = pass_timing(sim, prog, reps=1)
+        sim.reset()
+        sim.run(prog)
+        assert sim.sync() == 0
+        states[dt] = sim.state()
+        out[dt] = {"config": conf, "gates_per_s": len(g) / (step_ms / 1e3), "avg_launch_ms": launch_ms,
+                   "tflops": f / (launch_ms / 1e3) / 1e12}
+        prog.free()
+        sim.close()
+    a, b = states["c128"].astype(np.complex128), states["c64"].astype(np.complex128)
+    fid = abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+    peak = fp64_peak_tflops(torch)
+    out["infidelity_c64_vs_c128"] = float(1 - fid)
+    out["fp64_peak_tflops"] = peak
+    out["fp64_peak_source"] = "measured here: cuBLAS DGEMM 4096^3 (torch.matmul float64), best of 5"
+    out["c128"]["frac_of_fp64_peak"] = out["c128"]["tflops"] / peak
+    out["c128"]["flops_note"] = "8 FP64 flops per amplitude per rotation (algorithmic), per tile-pass launch"
+    return out
+
+
 def run_ours(args):
     world, rank, local = dist_setup()
-    import numpy as np
     import torch
     if world > 1:
         import torch.distributed as dist
@@ -274,6 +392,8 @@ def run_ours(args):
     else:
         cfg = dict(fusion=args.fusion, k_max=args.k_max, tile_bits=args.tile_bits or 13,
                    persistent=args.persistent)
+        if args.threads:
+            cfg["threads"] = args.threads
         if args.forced_low:
             cfg["forced_low"] = args.forced_low
     stream = torch.cuda.current_stream()
@@ -330,21 +450,23 @@ def run_ours(args):
         sim2.apply(c.gates[: min(c.G, 2_000_000)])
         sim2.sync()
         barrier()
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             sim2.reset()
             sim2.apply(c.gates)
             z2 = sim2.expect(zt)
             o2, p2 = sim2.outcomes()
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world)
-        e2e = {"value": aggregate(c.G * args.steps, world, dt), "unit": "gates/s",
+        e2e = {"value": aggregate(c.G * e2e_steps, world, dt), "unit": "gates/s", "steps": e2e_steps,
                "h2d_bytes_per_step": int(info["device_bytes"] + zt.nbytes),
                "d2h_bytes_per_step": int(zt.size * 8 + o2.nbytes + p2.nbytes + 64),
                "includes": "host fusion + scheduling (pipelined), program upload, kernels, read-back"}
         sim2.close()
 
     if rank != 0:
+        sim.close()
         return
     hbm_peak, src = peaks()
     l2_gbs = l2_copy_gbs(torch, n)
@@ -356,29 +478,20 @@ def run_ours(args):
     gbs = bytes_l / (avg_ms / 1e3) / 1e9 if avg_ms else 0.0
     alu_frac = tflops / FP32_PEAK_TFLOPS
     mem_frac = gbs / hbm_peak
-    if alu_frac >= mem_frac:
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": alu_frac, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": mem_frac,
-                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
-    # DRAM traffic of one launch from the ncu capture summarised in
-    # profiles/rot_pass_21q_c64_m12.md (that exact configuration only)
-    traffic, traffic_src = None, None
-    if (cfg.get("fusion") == 2 and cfg.get("tile_bits") == 12 and not cfg.get("threads")
-            and not cfg.get("persistent") and not cfg.get("forced_low")):
-        traffic = 16854528
-        traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, m = 12 "
-                       "(caches flushed before the launch: the state's cold read; writes stay in L2)")
-    roof.update({"traffic": traffic, "traffic_source": traffic_src,
-                 "kernel": "tile passes: k_rot_pass (register segments) and k_tile_pass",
-                 "avg_launch_ms": avg_ms,
-                 "launch_samples": prof["samples"], "algorithmic_bytes_per_launch": bytes_l,
-                 "algorithmic_flops_per_launch": flops_l, "memory_gbs": gbs,
-                 "memory_frac_of_hbm": mem_frac, "hbm_peak_gbs": hbm_peak,
-                 "l2_copy_gbs": l2_gbs, "frac_of_l2_copy": gbs / l2_gbs if l2_gbs else None,
-                 "l2_copy_source": "measured here: CUDA graph of 100 in-place copies of an L2-resident "
-                                   "buffer the size of the state (read + write bytes), best of 5"})
+    # The 16 MiB state stays in L2 for the whole step, so the bound of a pass
+    # (one read and one write of the state) is L2 bandwidth, measured live.
+    roof = {"bound": "l2", "achieved": gbs, "peak": l2_gbs, "unit": "GB/s", "frac": gbs / l2_gbs,
+            "peak_source": "measured here: CUDA graph of 100 in-place copies of an L2-resident buffer the "
+                           "size of the state (read + write bytes), best of 5",
+            "traffic": TRAFFIC_PER_LAUNCH if cfg == TRAFFIC_CONFIG else None,
+            "traffic_source": TRAFFIC_SOURCE if cfg == TRAFFIC_CONFIG else "no capture of this configuration",
+            "kernel": "tile passes: k_rot_pass (register segments) and k_tile_pass",
+            "avg_launch_ms": avg_ms, "launch_samples": prof["samples"],
+            "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
+            "frac_of_measured_hbm": mem_frac, "hbm_peak_gbs": hbm_peak,
+            "hbm_peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+            "alu_tflops": tflops, "frac_of_fp32_alu": alu_frac,
+            "fp32_alu_peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
     launches = args.steps * (info["passes"] + 2 * info["measurements"] + 1 + 2)
     sampling = {"shots": int(shots.size), "seconds": t_shots, "shots_per_s": shots.size / t_shots,
                 "includes": "FP64 prefix sums of the 2^21 Born weights, 1e6 Philox draws and searches, "
@@ -411,30 +524,56 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.cpu_seconds)
-    print(json.dumps(line), flush=True)
     sim.close()
+    if world == 1 and not args.no_summaries:
+        # side measurements (outside the timed region): the same recipe above L2
+        # size, the paper's complex128 arithmetic on a prefix, and the batched
+        # and serving workloads (their own lines, nested)
+        line["hbm_side"] = hbm_side(torch, cfg, hbm_peak, src)
+        line["precision_check"] = precision_check(torch, c, cfg)
+        nb = run_batched(argparse.Namespace(**{**vars(args), "steps": 3, "warmup": 3}), nested=True)
+        line["batched"] = {k: nb[k] for k in ("metric", "value", "unit", "ms_per_step", "gates_per_s", "e2e",
+                                               "fidelity", "c128_per_circuit", "roofline", "clocks",
+                                               "gpu_launches", "cpu_baseline")}
+        line["batched"]["config"] = {k: nb["config"][k] for k in ("workload", "instances", "resident_instances",
+                                                                  "tuned_config_by_width")}
+        ns = run_serving(argparse.Namespace(**{**vars(args), "serve_seconds": args.summary_serve_seconds}),
+                         nested=True)
+        line["serving"] = {k: ns[k] for k in ("metric", "value", "unit", "p50_ms", "p99_ms", "submitted",
+                                               "completed", "statuses", "offered_gates_per_s",
+                                               "served_gates_per_s", "saturated", "accuracy", "roofline",
+                                               "clocks", "gpu_launches", "config", "cpu_baseline")}
+    print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
+def run_batched(args, nested=False):
     """512 parameter sets of one 12-qubit 20,000-gate circuit + 256 circuits of width
     U{10..18}, complex64 (FP64 reductions), <H> of a 200-term Hamiltonian per instance.
-    A step = reset + every instance's full circuit + every <H>."""
-    world, rank, local = dist_setup()
-    import numpy as np
+    A step = reset + every instance's full circuit + every <H>.  The compile
+    configuration is autotuned per width group (--fusion -1) or forced.
+    nested: return the line (the caller owns the process group and device)."""
+    world, rank, local = (1, 0, 0) if nested else dist_setup()
     import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
+    from paper_2310_17739_gb300 import autotune
     from paper_2310_17739_gb300 import qsim as qs
     from paper_2310_17739_gb300 import workload as W
 
     cs, hams = W.config_batched()
     G = sum(c.G for c in cs)
-    fusion = 2 if args.fusion < 0 else args.fusion  # default: with gadget rotations
-    cfg = dict(fusion=fusion, k_max=args.k_max)
     stream = torch.cuda.current_stream()
-    b = qs.Batch([c.n for c in cs], "c64", stream=stream, config=cfg, seeds=[0] * len(cs))
+    b = qs.Batch([c.n for c in cs], "c64", stream=stream, seeds=[0] * len(cs))
+    t0 = time.perf_counter()
+    if args.fusion < 0:
+        tuned = autotune.tune_batch(b, cs, prefix=20_000, use_cache=False)
+    else:
+        tuned = {n: dict(fusion=args.fusion, k_max=args.k_max) for n in set(c.n for c in cs)}
+        for i, c in enumerate(cs):
+            b.set_instance_config(i, **tuned[c.n])
+    t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     b.compile_many([c.gates for c in cs])
     t_compile = time.perf_counter() - t0
@@ -490,7 +629,9 @@ def run_batched(args):
     # 8 * 2^k per dense k-qubit op), from the host compiler's op lists
     def prog_flops(c):
         """(algorithmic flops of one run, bytes of the uploaded device program)."""
-        ops = qs.fuse(c.n, c.gates, dtype=qs.C64, fusion=fusion, tile_bits=c.n if c.n <= 14 else 0)
+        conf = dict(tuned[c.n])
+        conf["tile_bits"] = c.n if c.n <= 14 else conf.get("tile_bits", 0)
+        ops = qs.fuse(c.n, c.gates, dtype=qs.C64, **conf)
         dense = [o for o in ops if isinstance(o[0], int)]
         n_rot = sum(1 for o in ops if o[0] in ("pauli", "frame"))
         fpa = 8 * n_rot + sum(8 << o[0] for o in dense)
@@ -499,7 +640,7 @@ def run_batched(args):
     f_set, b_set = prog_flops(cs[0])
     rest = [prog_flops(c) for c in cs[512:]]
     tiled = [c for c in cs if c.n > 14]
-    tiled_passes = sum(len(qs.schedule(c.n, c.gates, dtype=qs.C64, fusion=fusion)) for c in tiled)
+    tiled_passes = sum(len(qs.schedule(c.n, c.gates, dtype=qs.C64, **tuned[c.n])) for c in tiled)
     n_groups = len({c.n for c in cs if c.n <= 14})
     launches_per_step = n_groups + len(tiled) + tiled_passes + 1 + 2 * len(tiled)
     flops = f_set * 512 + sum(f for f, _ in rest)
@@ -521,13 +662,17 @@ def run_batched(args):
         f = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
         infid.append(1 - f)
         herr.append(float(np.abs(vals[i] - oracle.expect(ref, c.n, hams[i])).max()))
-    # plain complex128 per-circuit execution (paper fusion, one context, one circuit
-    # at a time) on a sample, extrapolated to the whole batch
+    # plain complex128 per-circuit execution (one context, one circuit at a time,
+    # each in its own autotuned complex128 configuration) on a sample,
+    # extrapolated to the whole batch
     t128 = 0.0
     samp128 = [0, 1, 512, 513, 514, 515]
+    cfg128 = {}
     for i in samp128:
         c = cs[i]
-        sim = qs.Sim(c.n, "c128", stream=stream, config=dict(fusion=1))
+        if c.n not in cfg128:
+            cfg128[c.n], _ = autotune.tune(c.n, c.gates, "c128", prefix=20_000, use_cache=False)
+        sim = qs.Sim(c.n, "c128", stream=stream, config=cfg128[c.n])
         p = sim.compile(c.gates)
         sim.run(p)
         sim.sync()
@@ -558,8 +703,8 @@ def run_batched(args):
                                "20,000 gates each; <H> of a 200-term Pauli Hamiltonian per instance",
                    "instances": len(cs), "gates_total": G,
                    "resident_instances": b.resident_count(),
-                   "fusion": "paper stages 1-4 + Pauli-gadget rotations" if fusion == 2 else "paper stages 1-4",
-                   "compile_s": t_compile,
+                   "tuned_config_by_width": {str(n): cfg for n, cfg in sorted(tuned.items())},
+                   "tune_s": t_tune, "compile_s": t_compile,
                    "l2": "flushed before the timed region"},
         "gates_per_s": G * args.steps * world / (ms / 1e3),
         "gpu_launches": args.steps * launches_per_step,
@@ -570,13 +715,16 @@ def run_batched(args):
                 "includes": "host compile of all 768 circuits, upload, run, <H> read-back"},
         "fidelity": {"sample": sample, "max_infidelity": max(infid), "max_abs_H_error": max(herr)},
         "c128_per_circuit": {"value": c128_rate, "unit": "circuits/s",
-                             "how": "complex128, paper fusion, one context per circuit, sequential; "
-                                    f"sample {samp128}", "speedup_of_batched_c64": value / c128_rate},
+                             "how": "complex128, one context per circuit, sequential, each width in its "
+                                    f"autotuned complex128 configuration {cfg128}; sample {samp128}",
+                             "speedup_of_batched_c64": value / c128_rate},
         "cpu_baseline": {"value": len(sample) / t_cpu, "unit": "circuits/s", "cores": 1,
                          "kind": "oracle", "sample": f"instances {sample}, complex128, unfused"},
     }
-    print(json.dumps(line), flush=True)
     b.close()
+    if nested:
+        return line
+    print(json.dumps(line), flush=True)
 
 
 def serving_pool(size, seed=5):
@@ -595,15 +743,16 @@ def serving_pool(size, seed=5):
     return pool
 
 
-def run_serving(args):
+def run_serving(args, nested=False):
     """Poisson arrivals (rate args.rate) for args.serve_seconds, served by the
-    continuous-admission loop; requests are drawn from a seeded pool."""
+    continuous-admission loop; requests are drawn from a seeded pool.
+    nested: return the line instead of printing it."""
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")  # slot streams on separate queues
-    world, rank, local = dist_setup()
-    import numpy as np
+    world, rank, local = (1, 0, 0) if nested else dist_setup()
     import torch
     torch.cuda.set_device(local)
     from paper_2310_17739_gb300 import qsim as qs
+    from paper_2310_17739_gb300 import workload as W
 
     pool = serving_pool(args.pool if hasattr(args, "pool") else 96)
     fusion = 2 if args.fusion < 0 else args.fusion
@@ -642,7 +791,7 @@ def run_serving(args):
             ta, pi = arrivals[k]
             c = pool[pi]
             rid = srv.submit(c.n, c.gates, seed=k, t_submit=t_start + ta)
-            meta[rid] = (pi, ta)
+            meta[rid] = (pi, ta, k)
             k += 1
         for r in srv.poll():
             results[r["id"]] = r
@@ -697,14 +846,27 @@ def run_serving(args):
     statuses = {}
     for r in results.values():
         statuses[r["status"]] = statuses.get(r["status"], 0) + 1
-    # CPU oracle on a sample of the smallest pool requests
+    # the CPU oracle on the served results of the smallest pool requests: the
+    # same seed (the arrival index), outcomes bit for bit, <Z_q> per result
     import oracle
     small = sorted(range(len(pool)), key=lambda i: pool[i].G * (1 << pool[i].n))[:4]
+    checked, z_err, match = [], 0.0, True
     ta = time.perf_counter()
-    for i in small:
-        psi = oracle.basis_state(pool[i].n)
-        oracle.run(psi, pool[i].n, pool[i].gates, seed=0)
-    cpu_rate = len(small) / (time.perf_counter() - ta)
+    for pi in small:
+        rid = next((i for i in sorted(results) if meta[i][0] == pi), None)
+        if rid is None:
+            continue
+        c = pool[pi]
+        seed_k = meta[rid][2]
+        psi = oracle.basis_state(c.n)
+        o = oracle.run(psi, c.n, c.gates, seed=seed_k)
+        r = results[rid]
+        bits = sum(int(b) << k for k, b in enumerate(o.outcomes[:64]))
+        match = match and r["outcomes"] == bits and r["status"] == 0
+        z_ref = oracle.expect(psi, c.n, W.z_terms(c.n))[: min(c.n, 32)]
+        z_err = max(z_err, float(np.abs(np.asarray(r["z"]) - z_ref).max()))
+        checked.append(int(rid))
+    cpu_rate = max(len(checked), 1) / (time.perf_counter() - ta)
     value = completed / window
     line = {
         "metric": "served circuits/s with p50/p99 latency (arrival to result)",
@@ -734,9 +896,15 @@ def run_serving(args):
                 "includes": "the whole loop is end to end: submit from host records, host compile, "
                             "upload, kernels, result read-back"},
         "server_counts": counts,
+        "accuracy": {"checked_requests": checked, "outcomes_match_oracle": bool(match),
+                     "max_abs_z_error": z_err,
+                     "how": "served results of the smallest pool requests against the CPU oracle "
+                            "(complex128, same seed): measurement outcomes and <Z_q> per result"},
         "cpu_baseline": {"value": cpu_rate, "unit": "circuits/s", "cores": 1, "kind": "oracle",
                          "sample": f"pool requests {small} (smallest work), complex128, unfused"},
     }
+    if nested:
+        return line
     print(json.dumps(line), flush=True)
 
 

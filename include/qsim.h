@@ -65,8 +65,9 @@ typedef enum {
     QSIM_E_OOM = 2,       /* device or host allocation failed */
     QSIM_E_CUDA = 3,      /* CUDA runtime error (message in qsim_last_error) */
     QSIM_E_ZEROPROB = 4,  /* assertion-mode measurement with P(0) <= threshold */
-    QSIM_E_TIMEOUT = 5,   /* a bounded device wait expired */
-    QSIM_E_STATE = 6      /* context unusable after an earlier failure */
+    QSIM_E_TIMEOUT = 5,   /* a bounded wait (qsim_sync_timeout) expired; the work goes on */
+    QSIM_E_STATE = 6,     /* context unusable after an earlier failure */
+    QSIM_E_CANCELED = 7   /* a served request cancelled before admission (qsim_server_cancel) */
 } qsim_status;
 
 /* ---------------------------------------------------------------- records --
@@ -158,9 +159,17 @@ typedef struct {
  *          other count, raised to m - 10 when below).  Fewer forced qubits
  *          leave more tile dimensions for rotations (fewer passes) at the cost
  *          of shorter contiguous rows.  Resident-block passes (persistent = 1)
- *          need 4 and fall back to one block per tile below that.
+ *          need 4 and fall back to one block per tile below that.  At most
+ *          4 for complex64 and 3 for complex128 (the longest contiguous row
+ *          the tile kernels use); larger values are rejected.
+ * struct_size  must equal sizeof(qsim_config) (qsim_config_init sets it):
+ *          every call that reads a qsim_config refuses one whose size field
+ *          differs (QSIM_E_INVAL), so a caller built against another layout
+ *          of this struct is told so instead of having memory past its struct
+ *          read or written.
  */
 typedef struct {
+    uint32_t struct_size;
     int32_t fusion;
     int32_t k_max;
     int32_t tile_bits;
@@ -172,6 +181,10 @@ typedef struct {
     int32_t graphs;
     int32_t forced_low;
 } qsim_config;
+
+/* The defaults (the paper's fusion, k_max 2, every other field 0 = automatic)
+ * with struct_size set.  Start every qsim_config from this. */
+QSIM_API void qsim_config_init(qsim_config *cfg);
 
 typedef struct {
     uint64_t gates;          /* input records */
@@ -301,6 +314,12 @@ QSIM_API qsim_status qsim_profile_read(qsim_ctx *ctx, double *sampled_ms, uint64
 
 /* Wait for all enqueued work; report deferred device errors. */
 QSIM_API qsim_status qsim_sync(qsim_ctx *ctx);
+/* qsim_sync with a bound on the host's wait: polls an event recorded behind
+ * the work enqueued so far and returns QSIM_E_TIMEOUT if it has not completed
+ * after `seconds` (>= 0).  On timeout nothing is cancelled: the work keeps
+ * running, the context stays usable, and a later qsim_sync or
+ * qsim_sync_timeout reports its outcome.  Otherwise as qsim_sync. */
+QSIM_API qsim_status qsim_sync_timeout(qsim_ctx *ctx, double seconds);
 QSIM_API const char *qsim_last_error(const qsim_ctx *ctx);
 QSIM_API const char *qsim_status_string(qsim_status s);
 
@@ -328,6 +347,10 @@ QSIM_API qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_
                                        void *user, qsim_batch **out);
 QSIM_API qsim_status qsim_batch_destroy(qsim_batch *b);
 QSIM_API qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg);
+/* The configuration of instance `index` alone (for example one tuned for its
+ * width); it applies to that instance's next qsim_batch_compile.  Instances
+ * run resident keep tile_bits = their n. */
+QSIM_API qsim_status qsim_batch_set_instance_config(qsim_batch *b, int index, const qsim_config *cfg);
 /* seeds[i]: draw seed of instance i (default 0). */
 QSIM_API qsim_status qsim_batch_set_seeds(qsim_batch *b, const uint64_t *seeds);
 /* Compile gates for instance `index` (host compiler) and upload the program,
@@ -399,7 +422,14 @@ QSIM_API qsim_status qsim_server_submit(qsim_server *s, int n_qubits, const qsim
                                         uint64_t seed, double t_submit, uint64_t *id);
 /* Move up to cap finished results into out; *n_out = how many. */
 QSIM_API qsim_status qsim_server_poll(qsim_server *s, qsim_result *out, size_t cap, size_t *n_out);
-/* Counters: submitted, admitted, completed, pending (not yet admitted), running. */
+/* Cancel a request that has not been admitted yet (still compiling, or
+ * waiting for a slot or memory): its result is delivered at once with status
+ * QSIM_E_CANCELED, t_admit = -1, and it never runs; the requests behind it
+ * keep their order.  QSIM_E_INVAL if `id` is not waiting (unknown, already
+ * admitted, finished or cancelled). */
+QSIM_API qsim_status qsim_server_cancel(qsim_server *s, uint64_t id);
+/* Counters: submitted, admitted, completed (results produced, cancelled ones
+ * included), pending (neither admitted nor cancelled), running. */
 QSIM_API qsim_status qsim_server_counts(const qsim_server *s, uint64_t *submitted, uint64_t *admitted,
                                         uint64_t *completed, uint64_t *pending, uint64_t *running);
 QSIM_API double qsim_server_now(const qsim_server *s);
@@ -420,7 +450,9 @@ QSIM_API double qsim_server_now(const qsim_server *s);
  * reduction's scratch is a fixed 16.25 KiB array in the library's device
  * memory, present on every GPU that loads the library until the process
  * exits.  Limits: 1 <= n_qubits <= 34 and 0 <= qubit < n_qubits, otherwise
- * QSIM_E_INVAL with nothing enqueued; QSIM_E_CUDA on a CUDA error.  The first
+ * QSIM_E_INVAL with nothing enqueued; d_state and stream must belong to the
+ * current CUDA device (QSIM_E_INVAL otherwise: the scratch used is that
+ * device's copy); QSIM_E_CUDA on a CUDA error.  The first
  * call on each device looks up the scratch array's address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  Every call on a device shares the scratch array, which
@@ -436,14 +468,17 @@ QSIM_API qsim_status qsim_prob_noalloc(const void *d_state, int n_qubits, qsim_d
  * in IBM OpenQASM").  Read: OPENQASM 2.x; include (qelib1 is built in);
  * qreg/creg (qubits numbered by declaration order, up to 64); the qelib1 gates
  * id x y z h s sdg t tdg rx ry rz u1 p u2 u3 u U cx CX cy cz ch swap crx cry crz
- * cu1 cp cu3 rxx rzz sx sxdg ccx cswap, applied to qubits or broadcast over
- * whole registers of one size; parameter expressions (numbers, pi, + - * / ^,
+ * cu1 cp cu3 rxx rzz sx sxdg ccx cswap c3x c4x c3sqrtx rccx rc3x, applied to
+ * qubits or broadcast over whole registers of one size; parameter expressions
+ * (numbers, pi, + - * / ^,
  * unary minus, sin cos tan exp ln sqrt); `gate` definitions (expanded in
  * place); measure (-> a declared creg), reset, barrier (a full barrier).  Not
- * read: opaque, if.  ccx and cswap become 1- and 2-qubit gates, sx and sxdg C1
- * records; gate matrices and global phases are the library's (see the record
- * definitions above).  Writes gates[0..*n_gates), mats[0..*n_mats) (doubles,
- * for the C1 records) and *n_qubits.  Two-call use: with capacities too small
+ * read: opaque, if.  ccx, cswap, rccx and rc3x become 1- and 2-qubit gates
+ * (rccx / rc3x with the relative phases of the OpenQASM 2.0 standard header),
+ * c3x, c4x and c3sqrtx exact controlled-X^t C2 records (X^(1/2) = the matrix of
+ * sx), sx and sxdg C1 records; gate matrices and global phases are the
+ * library's (see the record definitions above).  Writes gates[0..*n_gates),
+ * mats[0..*n_mats) (doubles, for the C1 / C2 records) and *n_qubits.  Two-call use: with capacities too small
  * it returns QSIM_E_INVAL after setting *n_gates and *n_mats.  Errors: a
  * message "line L: ..." in err (err_cap bytes, NUL-terminated), QSIM_E_INVAL;
  * QSIM_E_OOM when host memory runs out.  Host only. */

@@ -1,11 +1,15 @@
-"""Autotuner for the compile configuration (fusion level, k_max, tile size,
-threads per block).
+"""Autotuner for the compile configuration (fusion level, fused block width
+k_max, tile size, threads per block).
 
 Times each candidate configuration on a prefix of the caller's own gate stream
 through the C ABI (compile once, run twice, CUDA-event timed on the context's
-stream) and keeps the fastest.  Results are cached in a JSON file keyed by
-(GPU name, n, dtype, fusion family, prefix size), so a later run with the same
-key reuses the choice without timing.
+stream) and keeps the fastest.  Candidates: the paper's fusion (fusion 1) with
+dense blocks of up to k_max = 2..5 qubits (5 is the compiler's largest block),
+and Pauli-gadget rotations (fusion 2), at the three largest tile sizes.
+Results are cached in a JSON file keyed by (GPU name, n, dtype, fusion family,
+prefix size), so a later run with the same key reuses the choice without
+timing.  tune_batch tunes a batch per width group and applies each group's
+choice to its instances.
 """
 from __future__ import annotations
 
@@ -21,12 +25,18 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache
 def candidates(n: int, dtype: str, allow_rotations: bool = True):
     """Configurations worth timing for an n-qubit state."""
     mx = 14 if dtype == "c64" else 13
+    if n <= mx:  # the whole state in one block: the tile size is n
+        out = [dict(fusion=1, k_max=k, tile_bits=n) for k in (2, 3, 4, 5)]
+        if allow_rotations:
+            out.append(dict(fusion=2, k_max=2, tile_bits=n))
+        return out
     tiles = sorted({min(n, t) for t in (mx - 2, mx - 1, mx)})
     out = []
     for t in tiles:
-        out.append(dict(fusion=1, k_max=2, tile_bits=t))
-        out.append(dict(fusion=1, k_max=3, tile_bits=t))
-        out.append(dict(fusion=1, k_max=4, tile_bits=t))
+        for k in (2, 3, 4, 5):
+            out.append(dict(fusion=1, k_max=k, tile_bits=t))
+        if dtype == "c64":  # twice the warps per block (a 14-dimensional tile fills an SM's shared memory)
+            out.append(dict(fusion=1, k_max=2, tile_bits=t, threads=512))
         if allow_rotations:
             out.append(dict(fusion=2, k_max=2, tile_bits=t))
             if dtype == "c64":
@@ -98,3 +108,20 @@ def tune(n: int, gates, dtype: str = "c64", prefix: int = 1_000_000, allow_rotat
     except OSError:
         pass
     return best, entry
+
+
+def tune_batch(batch, circuits, dtype: str = "c64", allow_rotations: bool = True, prefix: int = 200_000,
+               use_cache: bool = True):
+    """Tune once per distinct width of a batch (on the first instance of that
+    width, through a single-state context) and set that configuration on every
+    instance of the width (qsim_batch_set_instance_config); compile afterwards.
+    Returns {n: best_config}."""
+    first = {}
+    for i, c in enumerate(circuits):
+        first.setdefault(batch.n[i], c)
+    best = {}
+    for n, c in sorted(first.items()):
+        best[n], _ = tune(n, c.gates, dtype, prefix=prefix, allow_rotations=allow_rotations, use_cache=use_cache)
+    for i in range(len(batch)):
+        batch.set_instance_config(i, **best[batch.n[i]])
+    return best

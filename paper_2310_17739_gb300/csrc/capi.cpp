@@ -61,6 +61,24 @@ struct DevChunk {
     uint64_t measurements = 0;
 };
 
+// Whether the 2^k x 2^k matrix at M (row-major) has at most one nonzero entry
+// per row; if so perm gets that entry's column for row r at bits 2r..2r+1.
+bool monomial(const cd *M, int k, uint16_t *perm) {
+    const int D = 1 << k;
+    uint16_t p = 0;
+    for (int r = 0; r < D; r++) {
+        int col = -1;
+        for (int c = 0; c < D; c++) {
+            if (M[r * D + c] == cd(0.0, 0.0)) continue;
+            if (col >= 0) return false;
+            col = c;
+        }
+        if (col > 0) p |= (uint16_t)(col << (2 * r));
+    }
+    *perm = p;
+    return true;
+}
+
 void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
     pk.n = hp.n;
     pk.m = hp.m;
@@ -138,11 +156,19 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
         };
         std::vector<DevOp> body;
         bool all_rot = true;
+        bool regable = true;    // every op fits a register segment (rotation or dense k <= 2)
+        bool has_dense = false;
+        uint32_t mono_saved = 0;  // algorithmic flops per amplitude saved by monomial ops
+        double gprod = 1.0;       // product of the cosines of the rotations in scaled form
         auto emit_body = [&]() {
             qsim::Subspace S;
             for (int j = 0; j < m; j++) S.add(B[j]);
             body.clear();
             all_rot = true;
+            regable = true;
+            has_dense = false;
+            mono_saved = 0;
+            gprod = 1.0;
             for (uint64_t i = src.first; i < src.first + src.count; i++) {
                 const qsim::FOp &o = hp.ops[i];
                 DevOp d;
@@ -166,17 +192,40 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                     d.flags = (uint16_t)(zc & 0xffff);
                     d.pad = (uint16_t)(zc >> 16);
                     const cd cs = hp.pool[o.mat];
-                    set_coef(o.mat, cs.real(), e >= 2 ? -cs.imag() : cs.imag());
-                    if (__builtin_popcount(lx) > 5) all_rot = false;
+                    const double w = e >= 2 ? -cs.imag() : cs.imag();
+                    // scaled form in tile passes (not in the resident kernel):
+                    // a' = a + (W / cos) (...), the cosine applied at write-back;
+                    // only while the running product stays >= 2^-40, so that the
+                    // unscaled amplitudes cannot grow beyond 2^40
+                    if (!hp.resident && std::fabs(cs.real()) >= 0.5 &&
+                        std::fabs(gprod * cs.real()) >= 0x1p-40) {
+                        set_coef(o.mat, cs.real(), w / cs.real());
+                        d.lq[4] |= 2;
+                        gprod *= cs.real();
+                    } else {
+                        set_coef(o.mat, cs.real(), w);
+                    }
+                    if (__builtin_popcount(lx) > 5) all_rot = regable = false;
                 } else {
                     for (int j = 0; j < o.k; j++) d.lq[j] = (uint8_t)__builtin_ctz(S.coords(1ull << o.q[j]));
+                    uint16_t perm = 0;
+                    if (o.k <= 2 && monomial(hp.pool.data() + o.mat, o.k, &perm)) {
+                        d.k = o.k == 1 ? qsim::kMono1 : qsim::kMono2;
+                        d.flags = perm;
+                        mono_saved += (8u << o.k) - 8u;
+                    }
                     all_rot = false;
+                    has_dense = true;
+                    if (o.k > 2) regable = false;
                 }
                 body.push_back(d);
             }
         };
         emit_body();
-        bool reg = allow_reg && reg_dtype && all_rot && src.gadget && hp.n <= 32;
+        // register segments: a rotation-only pass over its gadget basis, or any
+        // pass whose ops are rotations with <= 5 X coordinates and dense ops of
+        // <= 2 qubits
+        bool reg = allow_reg && reg_dtype && hp.n <= 32 && (src.gadget ? all_rot : regable);
         // the generic tile kernel wants the basis vectors after the leading
         // unit ones free of those low bits (whole 16-byte runs per row)
         auto reduce_basis = [&]() {
@@ -189,13 +238,16 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             // scaled form: every cosine is >= 1/sqrt(2) after the Pauli frame
             double scale = 1.0;
             for (uint64_t i = src.first; i < src.first + src.count && reg; i++) {
+                if (!hp.ops[i].pauli()) continue;
                 const cd cs = hp.pool[hp.ops[i].mat];
                 if (std::fabs(cs.real()) < 0.5) reg = false;
                 scale *= cs.real();
+                if (std::fabs(scale) < 0x1p-40) reg = false;  // unscaled amplitudes would grow beyond 2^40
             }
             if (reg) {
                 for (uint64_t i = src.first; i < src.first + src.count; i++) {
                     const qsim::FOp &o = hp.ops[i];
+                    if (!o.pauli()) continue;
                     const cd cs = hp.pool[o.mat];
                     const int e = (__builtin_popcountll(o.xm & o.zm) + 3 + (o.flags & qsim::kPhaseMask)) & 3;
                     const double w = e >= 2 ? -cs.imag() : cs.imag();
@@ -220,13 +272,58 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             for (uint32_t q = 0; q < src.mat_count; q++) tvals[q] = tvals_f[2 * (src.mat_first + q) + 1];
             uint32_t R = 0;
             std::vector<DevOp> cur;
+            std::vector<size_t> cur_ix;  // body index of each op of cur
+            // tile positions an op needs in registers: a rotation's X
+            // coordinates, a dense op's qubits
+            auto need = [&](const DevOp &d) -> uint32_t {
+                if (d.k == qsim::kPauli) return d.lq[0] | ((uint32_t)d.lq[1] << 8);
+                const int k = (d.k == 1 || d.k == qsim::kMono1) ? 1 : 2;
+                uint32_t r = 1u << d.lq[0];
+                if (k == 2) r |= 1u << d.lq[1];
+                return r;
+            };
             auto close = [&]() {
                 if (cur.empty()) return;
                 for (int b = m - 1; b >= 0 && __builtin_popcount(R) < 5; b--) R |= 1u << b;
                 int pos[5];
                 for (int b = 0, j = 0; b < 32; b++)
                     if ((R >> b) & 1) pos[j++] = b;
-                for (DevOp &d : cur) {
+                for (size_t ci = 0; ci < cur.size(); ci++) {
+                    DevOp &d = cur[ci];
+                    if (d.k != qsim::kPauli) {
+                        // dense op: its slots, its matrix (local bit 0 <-> the lower slot)
+                        const qsim::FOp &o = hp.ops[src.first + cur_ix[ci]];
+                        const bool mono = d.k == qsim::kMono1 || d.k == qsim::kMono2;
+                        const int k = (d.k == 1 || d.k == qsim::kMono1) ? 1 : 2, D = 1 << k;
+                        int sl[2] = {0, 0};
+                        for (int j = 0; j < k; j++)
+                            for (int t = 0; t < 5; t++)
+                                if (pos[t] == d.lq[j]) sl[j] = t;
+                        const bool swap = k == 2 && sl[0] > sl[1];
+                        auto sig = [&](int l) { return swap ? ((l & 1) << 1) | ((l >> 1) & 1) : l; };
+                        cd M[16];
+                        uint16_t perm = 0;
+                        for (int r = 0; r < D; r++)
+                            for (int c = 0; c < D; c++) M[sig(r) * D + sig(c)] = hp.pool[o.mat + (uint64_t)(r * D + c)];
+                        if (mono)
+                            for (int r = 0; r < D; r++)
+                                perm |= (uint16_t)(sig((d.flags >> (2 * r)) & 3) << (2 * sig(r)));
+                        const int s0 = std::min(sl[0], sl[1]), s1 = std::max(sl[0], sl[1]);
+                        static const int pair_no[5][5] = {{-1, 0, 1, 2, 3}, {0, -1, 4, 5, 6}, {1, 4, -1, 7, 8},
+                                                          {2, 5, 7, -1, 9}, {3, 6, 8, 9, -1}};
+                        qsim::RegDense rd;
+                        std::memset(&rd, 0, sizeof(rd));
+                        rd.k = qsim::kDenseReg;
+                        rd.sel = (uint8_t)(k == 1 ? (mono ? 15 : 0) + sl[0] : (mono ? 20 : 5) + pair_no[s0][s1]);
+                        rd.perm = perm;
+                        rd.tab = (uint32_t)tab.size();
+                        for (int q = 0; q < D * D; q++) {
+                            tab.push_back((float)M[q].real());
+                            tab.push_back((float)M[q].imag());
+                        }
+                        std::memcpy(&d, &rd, sizeof(d));
+                        continue;
+                    }
                     const uint32_t x = d.lq[0] | ((uint32_t)d.lq[1] << 8);
                     const uint32_t z = d.lq[2] | ((uint32_t)d.lq[3] << 8);
                     uint32_t xr = 0, zr = 0;
@@ -256,6 +353,7 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                 }
                 segs.emplace_back(R, cur);
                 cur.clear();
+                cur_ix.clear();
                 R = 0;
             };
             // List scheduling over the pass's rotations: an op is ready once
@@ -277,7 +375,7 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                 int best = -1, best_grow = 6;
                 for (size_t a = 0; a < K; a++) {
                     if (placed[a] || waits[a]) continue;
-                    const uint32_t x = body[a].lq[0] | ((uint32_t)body[a].lq[1] << 8);
+                    const uint32_t x = need(body[a]);
                     const int grow = __builtin_popcount(x & ~R);
                     if (__builtin_popcount(R | x) <= 5 && grow < best_grow) {
                         best = (int)a;
@@ -289,8 +387,9 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                     close();
                     continue;
                 }
-                R |= body[best].lq[0] | ((uint32_t)body[best].lq[1] << 8);
+                R |= need(body[best]);
                 cur.push_back(body[best]);
+                cur_ix.push_back((size_t)best);
                 placed[best] = 1;
                 for (uint32_t b : succ[best]) waits[b]--;
                 left--;
@@ -314,8 +413,9 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                     pk.ops.push_back(mk);
                     pk.ops.insert(pk.ops.end(), sg.second.begin(), sg.second.end());
                 }
-                p.reg = 1;
+                p.reg = has_dense ? 2 : 1;
                 p.count = (uint32_t)(pk.ops.size() - p.first);
+                p.fpa -= std::min(p.fpa, mono_saved);
                 pk.passes.push_back(p);
                 continue;
             }
@@ -327,6 +427,8 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
         }
         pk.ops.insert(pk.ops.end(), body.begin(), body.end());
         p.count = (uint32_t)(pk.ops.size() - p.first);
+        p.fpa -= std::min(p.fpa, mono_saved);
+        p.gscale = gprod;
         pk.passes.push_back(p);
     }
     pk.fused = fused;
@@ -385,6 +487,7 @@ struct qsim_ctx {
     cudaStream_t cap_stream = nullptr;    // private stream for graph capture (nothing runs on it)
     // graphs launched by qsim_apply, destroyed once the event after them has completed
     std::deque<std::pair<cudaEvent_t, std::vector<cudaGraphExec_t>>> graph_retire;
+    cudaEvent_t sync_ev = nullptr;        // qsim_sync_timeout: recorded behind the enqueued work
 };
 
 // A run of consecutive tile passes of one chunk (no measurement between
@@ -617,10 +720,10 @@ cudaError_t launch_tile(qsim_ctx *c, const DevChunk &dc, const Pass &p, int thre
     const uint64_t *basis = dc.bvec.data() + p.basis;
     if (p.reg)
         return qsim::launch_rot_pass(c->state, c->n, dc.m, p.tile, basis, dc.d_ops + p.first, p.count, dc.d_mats,
-                                     (uint32_t)p.mat_first, p.mat_count, p.scale, c->ctl, s);
+                                     (uint32_t)p.mat_first, p.mat_count, p.scale, p.reg == 2, c->ctl, s);
     return qsim::launch_tile_pass(c->dtype, threads, dc.kmax, c->state, c->n, dc.m, p.tile, basis,
                                   dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first, p.mat_count,
-                                  c->ctl, s);
+                                  p.gscale, c->ctl, s);
 }
 
 qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
@@ -662,7 +765,7 @@ qsim_status launch_chunk(qsim_ctx *c, const DevChunk &dc) {
             c->prof_in_window = 0;
         }
         const uint64_t *pb = dc.bvec.data() + p.basis;
-        if (p.reg && c->cfg.persistent && dc.m <= 13 && pb[0] == 1 && pb[1] == 2 && pb[2] == 4 && pb[3] == 8) {
+        if (p.reg == 1 && c->cfg.persistent && dc.m <= 13 && pb[0] == 1 && pb[1] == 2 && pb[2] == 4 && pb[3] == 8) {
             const uint64_t *basis = pb;
             if (!c->tile_ctr) {
                 c->tile_ctr = (unsigned long long *)dalloc(c, sizeof(unsigned long long));
@@ -966,6 +1069,30 @@ void accumulate(qsim_program_info &info, const Packed &pk, size_t dev_bytes) {
     for (int k = 0; k < 8; k++) info.op_hist[k] += pk.hist[k];
 }
 
+// Every field of a caller's qsim_config in its documented range (n = 0: the
+// state size is not known yet, so the tile_bits / n relation is not checked).
+bool check_config(const qsim_config *cfg, qsim_dtype dtype, int n, std::string &err) {
+    if (cfg->struct_size != sizeof(qsim_config)) {
+        err = "qsim_config.struct_size is " + std::to_string(cfg->struct_size) + ", this library's qsim_config has " +
+              std::to_string(sizeof(qsim_config)) + " bytes (initialise it with qsim_config_init)";
+        return false;
+    }
+    const int mx = qsim::max_resident_bits(dtype);
+    if (cfg->fusion < 0 || cfg->fusion > 2) err = "fusion must be 0, 1 or 2";
+    else if (cfg->k_max != 0 && (cfg->k_max < 2 || cfg->k_max > 5)) err = "k_max must be 0 or in [2, 5]";
+    else if (cfg->tile_bits < 0 || cfg->tile_bits > mx) err = "tile_bits out of range for this dtype";
+    else if (n > 0 && cfg->tile_bits > 0 && cfg->tile_bits < n && cfg->tile_bits < 6)
+        err = "tile_bits must be >= 6 unless it covers the whole state";
+    else if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512) err = "threads must be 0, 256 or 512";
+    else if (cfg->chunk_gates < 0 || cfg->lookahead < 0 || cfg->compile_threads < 0) err = "negative size";
+    else if (cfg->persistent != 0 && cfg->persistent != 1) err = "persistent must be 0 or 1";
+    else if (cfg->graphs < 0 || cfg->graphs > 2) err = "graphs must be 0, 1 or 2";
+    else if (cfg->forced_low < 0 || cfg->forced_low > (dtype == QSIM_C64 ? 4 : 3))
+        err = dtype == QSIM_C64 ? "forced_low must be in [0, 4] for complex64" : "forced_low must be in [0, 3] for complex128";
+    else return true;
+    return false;
+}
+
 }  // namespace
 
 extern "C" {
@@ -979,6 +1106,7 @@ const char *qsim_status_string(qsim_status s) {
         case QSIM_E_ZEROPROB: return "assertion failed: P(0) <= threshold";
         case QSIM_E_TIMEOUT: return "timeout";
         case QSIM_E_STATE: return "context unusable";
+        case QSIM_E_CANCELED: return "request cancelled";
     }
     return "unknown status";
 }
@@ -1055,6 +1183,7 @@ qsim_status qsim_destroy(qsim_ctx *c) {
     }
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->sync_ev) cudaEventDestroy(c->sync_ev);
     for (auto &e : c->prof_ev) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -1073,23 +1202,15 @@ qsim_status qsim_set_stream(qsim_ctx *c, void *stream) {
     return QSIM_OK;
 }
 
+void qsim_config_init(qsim_config *cfg) {
+    if (!cfg) return;
+    qsim::config_to(Config(), cfg);
+}
+
 qsim_status qsim_set_config(qsim_ctx *c, const qsim_config *cfg) {
     if (!c || !cfg) return fail(c, QSIM_E_INVAL, "null argument");
-    if (cfg->fusion < 0 || cfg->fusion > 2) return fail(c, QSIM_E_INVAL, "fusion must be 0, 1 or 2");
-    if (cfg->k_max != 0 && (cfg->k_max < 2 || cfg->k_max > 5))
-        return fail(c, QSIM_E_INVAL, "k_max must be 0 or in [2, 5]");
-    const int mx = qsim::max_resident_bits(c->dtype);
-    if (cfg->tile_bits < 0 || cfg->tile_bits > mx)
-        return fail(c, QSIM_E_INVAL, "tile_bits out of range for this dtype");
-    if (cfg->tile_bits > 0 && cfg->tile_bits < c->n && cfg->tile_bits < 6)
-        return fail(c, QSIM_E_INVAL, "tile_bits must be >= 6 unless it covers the whole state");
-    if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
-        return fail(c, QSIM_E_INVAL, "threads must be 0, 256 or 512");
-    if (cfg->chunk_gates < 0 || cfg->lookahead < 0 || cfg->compile_threads < 0)
-        return fail(c, QSIM_E_INVAL, "negative size");
-    if (cfg->persistent != 0 && cfg->persistent != 1) return fail(c, QSIM_E_INVAL, "persistent must be 0 or 1");
-    if (cfg->graphs < 0 || cfg->graphs > 2) return fail(c, QSIM_E_INVAL, "graphs must be 0, 1 or 2");
-    if (cfg->forced_low < 0 || cfg->forced_low > 8) return fail(c, QSIM_E_INVAL, "forced_low must be in [0, 8]");
+    std::string err;
+    if (!check_config(cfg, c->dtype, c->n, err)) return fail(c, QSIM_E_INVAL, err);
     c->cfg = qsim::config_from(cfg);
     c->cfg_gen++;
     return QSIM_OK;
@@ -1388,6 +1509,28 @@ qsim_status qsim_sync(qsim_ctx *c) {
     return sync_read(c);
 }
 
+qsim_status qsim_sync_timeout(qsim_ctx *c, double seconds) {
+    qsim_status s = check_usable(c);
+    if (s != QSIM_OK) return s;
+    if (!(seconds >= 0)) return fail(c, QSIM_E_INVAL, "seconds must be >= 0");
+    if (!c->sync_ev) CK(cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming), "event create");
+    CK(cudaEventRecord(c->sync_ev, c->stream), "event record");
+    const double t_end = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() +
+                         seconds;
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(c->sync_ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "event query");
+        const double now = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+        if (now >= t_end)
+            return fail(c, QSIM_E_TIMEOUT, "the enqueued work had not completed after " + std::to_string(seconds) +
+                                               " s (it keeps running)");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaGetLastError();  // cudaErrorNotReady from the queries
+    return sync_read(c);  // completed: reads the control block without waiting
+}
+
 qsim_status qsim_profile_start(qsim_ctx *c, int every) {
     qsim_status s = check_usable(c);
     if (s != QSIM_OK) return s;
@@ -1436,7 +1579,9 @@ qsim_status qsim_fuse(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng, co
                       uint64_t *out_mat, size_t cap_ops, double *out_mats, size_t cap_mat_doubles,
                       size_t *n_ops, size_t *n_mat_doubles) {
     if (n < 1 || n > 34 || (ng && !g)) return fail(nullptr, QSIM_E_INVAL, "bad arguments");
+    if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(nullptr, QSIM_E_INVAL, "bad dtype");
     std::string err;
+    if (cfg && !check_config(cfg, dtype, n, err)) return fail(nullptr, QSIM_E_INVAL, err);
     if (!qsim::validate(n, g, ng, mats, nm, err)) return fail(nullptr, QSIM_E_INVAL, err);
     HostProgram hp;
     qsim::compile(n, dtype, qsim::config_from(cfg), g, ng, mats, nm, hp);
@@ -1475,7 +1620,9 @@ qsim_status qsim_schedule(int n, qsim_dtype dtype, const qsim_gate *g, size_t ng
                           size_t nm, const qsim_config *cfg, uint64_t *out_tile, uint64_t *out_first,
                           uint32_t *out_count, uint64_t *out_basis, size_t cap, size_t *n_passes) {
     if (n < 1 || n > 34 || (ng && !g)) return fail(nullptr, QSIM_E_INVAL, "bad arguments");
+    if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(nullptr, QSIM_E_INVAL, "bad dtype");
     std::string err;
+    if (cfg && !check_config(cfg, dtype, n, err)) return fail(nullptr, QSIM_E_INVAL, err);
     if (!qsim::validate(n, g, ng, mats, nm, err)) return fail(nullptr, QSIM_E_INVAL, err);
     HostProgram hp;
     qsim::compile(n, dtype, qsim::config_from(cfg), g, ng, mats, nm, hp);
@@ -1637,6 +1784,8 @@ qsim_status qsim_batch_create(int count, const int32_t *n_qubits, qsim_dtype dty
 
 qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg) {
     if (!b || !cfg) return bfail(b, QSIM_E_INVAL, "null argument");
+    if (cfg->struct_size != sizeof(qsim_config))  // before copying the caller's struct
+        return bfail(b, QSIM_E_INVAL, "qsim_config.struct_size does not match this library (use qsim_config_init)");
     b->drop_graph();
     for (int i = 0; i < b->count; i++) {
         qsim_config c2 = *cfg;
@@ -1645,6 +1794,17 @@ qsim_status qsim_batch_set_config(qsim_batch *b, const qsim_config *cfg) {
         if (s != QSIM_OK) return bfail(b, s, b->inst[i]->err);
     }
     return QSIM_OK;
+}
+
+qsim_status qsim_batch_set_instance_config(qsim_batch *b, int index, const qsim_config *cfg) {
+    if (!b || !cfg || index < 0 || index >= b->count) return bfail(b, QSIM_E_INVAL, "bad batch index or null config");
+    if (cfg->struct_size != sizeof(qsim_config))
+        return bfail(b, QSIM_E_INVAL, "qsim_config.struct_size does not match this library (use qsim_config_init)");
+    b->drop_graph();
+    qsim_config c2 = *cfg;
+    if (b->resident[index]) c2.tile_bits = b->inst[index]->n;  // residency is fixed at create
+    qsim_status s = qsim_set_config(b->inst[index], &c2);
+    return s == QSIM_OK ? QSIM_OK : bfail(b, s, b->inst[index]->err);
 }
 
 qsim_status qsim_batch_set_seeds(qsim_batch *b, const uint64_t *seeds) {
@@ -1779,6 +1939,7 @@ qsim_status build_tiled_plan(qsim_batch *b, bool may_upload) {
                                               p.mat_count, ic->ctl, &a) ||
                         !qsim::generic_tile_ok(a))
                         return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernel");
+                    a.wscale = p.gscale;
                     a.pad = (uint32_t)std::max(dc.kmax, 1);  // op size, read back below
                     b->tiled_descs.push_back(a);
                     st.count++;
@@ -1989,13 +2150,20 @@ qsim_status qsim_batch_expect(qsim_batch *b, const qsim_pauli_term *terms, const
     std::vector<qsim::ExpectJob> jobs;
     for (int i = 0; i < b->count; i++) {
         if (!b->resident[i] || off[i + 1] == off[i]) continue;
-        qsim::ExpectJob j;
-        j.state = b->inst[i]->state;
-        j.terms = d_terms + 3 * off[i];
-        j.out = d_out + off[i];
-        j.n_terms = (uint32_t)(off[i + 1] - off[i]);
-        j.n = b->inst[i]->n;
-        jobs.push_back(j);
+        // one block per run of terms, at most 2^20 amplitude-terms each, so a
+        // wide instance's terms spread over several SMs (each term is still
+        // summed by one block in the same order)
+        const int n = b->inst[i]->n;
+        const uint64_t per = std::max<uint64_t>(1, (1ull << 20) >> n);
+        for (uint64_t t0 = off[i]; t0 < off[i + 1]; t0 += per) {
+            qsim::ExpectJob j;
+            j.state = b->inst[i]->state;
+            j.terms = d_terms + 3 * t0;
+            j.out = d_out + t0;
+            j.n_terms = (uint32_t)std::min<uint64_t>(per, off[i + 1] - t0);
+            j.n = n;
+            jobs.push_back(j);
+        }
     }
     qsim::ExpectJob *d_jobs = (qsim::ExpectJob *)dalloc(c, std::max<size_t>(jobs.size(), 1) * sizeof(qsim::ExpectJob));
     qsim_status s = (d_terms && d_out && d_jobs) ? QSIM_OK : bfail(b, QSIM_E_OOM, "expectation buffers");
@@ -2067,6 +2235,7 @@ struct ServerReq {
     std::vector<Packed> chunks;
     size_t device_bytes = 0;
     uint64_t n_meas = 0;
+    bool cancelled = false;  // its result was delivered by qsim_server_cancel; it never runs
 };
 
 struct Slot {
@@ -2144,9 +2313,10 @@ struct qsim_server {
     std::condition_variable cv_work, cv_sched;
     std::deque<std::unique_ptr<ServerReq>> pending;               // to compile
     std::vector<std::unique_ptr<ServerReq>> ready;                // compiled, by id - first_ready_id
+    std::vector<ServerReq *> compiling;                           // taken by a compile worker
     uint64_t next_id = 1, next_admit = 1;
     std::vector<qsim_result> results;
-    std::atomic<uint64_t> submitted{0}, admitted{0}, completed{0}, running{0};
+    std::atomic<uint64_t> submitted{0}, admitted{0}, completed{0}, running{0}, cancelled{0};
     std::vector<std::thread> workers;
     std::thread sched;
     std::atomic<bool> stop{false};
@@ -2164,6 +2334,17 @@ void server_compile_loop(qsim_server *s) {
             if (s->stop.load()) return;
             r = std::move(s->pending.front());
             s->pending.pop_front();
+            if (!r->cancelled) s->compiling.push_back(r.get());
+        }
+        if (r->cancelled) {  // nothing to compile: the scheduler drops it in its turn
+            std::vector<qsim_gate>().swap(r->gates);
+            std::vector<double>().swap(r->mats);
+            std::lock_guard<std::mutex> lk(s->mu);
+            const uint64_t idx = r->id - s->next_admit;
+            if (s->ready.size() <= idx) s->ready.resize(idx + 1);
+            s->ready[idx] = std::move(r);
+            s->cv_sched.notify_all();
+            continue;
         }
         Config c = s->cfg;
         if (r->n <= qsim::max_resident_bits(s->dtype)) c.tile_bits = r->n;  // one block per request
@@ -2180,6 +2361,7 @@ void server_compile_loop(qsim_server *s) {
         std::vector<double>().swap(r->mats);
         {
             std::lock_guard<std::mutex> lk(s->mu);
+            s->compiling.erase(std::find(s->compiling.begin(), s->compiling.end(), r.get()));
             const uint64_t idx = r->id - s->next_admit;  // ready[k] holds id next_admit + k
             if (s->ready.size() <= idx) s->ready.resize(idx + 1);
             s->ready[idx] = std::move(r);
@@ -2297,6 +2479,12 @@ void server_sched_loop(qsim_server *s) {
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 if (s->ready.empty() || !s->ready.front()) break;  // strict arrival order
+                if (s->ready.front()->cancelled) {  // its result is out already
+                    s->ready.erase(s->ready.begin());
+                    s->next_admit++;
+                    progress = true;
+                    continue;
+                }
                 const size_t need = s->ready.front()->device_bytes;
                 const bool alone = s->running.load() == 0;
                 if (need > s->budget - s->in_use && !alone) break;  // wait for memory to free up
@@ -2358,6 +2546,10 @@ qsim_status qsim_server_create(int slots, size_t mem_budget, qsim_dtype dtype, c
     *out = nullptr;
     if (slots < 1 || slots > 64) return fail(nullptr, QSIM_E_INVAL, "slots must be in [1, 64]");
     if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(nullptr, QSIM_E_INVAL, "bad dtype");
+    {
+        std::string err;
+        if (cfg && !check_config(cfg, dtype, 0, err)) return fail(nullptr, QSIM_E_INVAL, err);
+    }
     auto s = std::make_unique<qsim_server>();
     s->dtype = dtype;
     s->cfg = qsim::config_from(cfg);
@@ -2460,7 +2652,35 @@ qsim_status qsim_server_counts(const qsim_server *s, uint64_t *submitted, uint64
     if (admitted) *admitted = adm;
     if (completed) *completed = done;
     if (running) *running = s->running.load();
-    if (pending) *pending = sub >= adm ? sub - adm : 0;
+    const uint64_t can = s->cancelled.load();
+    if (pending) *pending = sub >= adm + can ? sub - adm - can : 0;
+    return QSIM_OK;
+}
+
+qsim_status qsim_server_cancel(qsim_server *s, uint64_t id) {
+    if (!s) return fail(nullptr, QSIM_E_INVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    ServerReq *r = nullptr;
+    for (auto &p : s->pending)
+        if (p->id == id) r = p.get();
+    for (ServerReq *p : s->compiling)
+        if (p->id == id) r = p;
+    if (!r && id >= s->next_admit && id - s->next_admit < s->ready.size() && s->ready[id - s->next_admit])
+        r = s->ready[id - s->next_admit].get();
+    if (!r || r->cancelled) return fail(nullptr, QSIM_E_INVAL, "request " + std::to_string(id) + " is not waiting");
+    r->cancelled = true;
+    qsim_result res;
+    std::memset(&res, 0, sizeof(res));
+    res.id = r->id;
+    res.status = QSIM_E_CANCELED;
+    res.n_qubits = r->n;
+    res.success = 1.0;
+    res.t_submit = r->t_submit;
+    res.t_admit = -1.0;
+    res.t_done = steady_now() - s->t0;
+    s->results.push_back(res);
+    s->cancelled++;
+    s->completed++;
     return QSIM_OK;
 }
 

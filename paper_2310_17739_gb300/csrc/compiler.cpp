@@ -397,6 +397,7 @@ Config config_from(const qsim_config *c) {
 
 void config_to(const Config &c, qsim_config *o) {
     std::memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(qsim_config);
     o->fusion = c.fusion;
     o->k_max = c.k_max;
     o->tile_bits = c.tile_bits;

@@ -125,7 +125,8 @@ struct Pass {
     uint64_t first = 0;
     uint32_t count = 0;
     uint8_t ev = EV_NONE;
-    uint8_t reg = 0;      // laid out in register segments (set when packed for the device)
+    uint8_t reg = 0;      // register segments (set when packed for the device): 1 rotations only,
+                          // 2 with dense ops (RegDense)
     uint16_t flags = 0;   // event flags (bit 0: assertion mode)
     uint32_t q = 0;       // event qubit
     uint32_t fpa = 0;     // algorithmic real flops per amplitude of the pass (8 * 2^k per op)
@@ -135,6 +136,7 @@ struct Pass {
     uint8_t gadget = 0;   // basis = X masks of its rotations in order (rotation-only pass);
                           // otherwise the reduced row-echelon basis, ascending pivots
     float scale = 1.0f;   // register-segment passes: product of the rotations' cosines
+    double gscale = 1.0;  // generic passes: product of the cosines of the rotations in scaled form
 };
 
 // Per-pass limits of the tile kernel (its ops and coefficients are copied

@@ -9,8 +9,9 @@
 //                   whole instruction stream -- dense ops, measurements, resets
 //                   -- runs in one launch (one block per state for batches).
 //   k_prob          FP64 Born probabilities of one qubit: per-block partials,
-//                   then the last block to arrive sums them in block order,
-//                   draws (or asserts) the outcome and writes the scale.
+//                   then the last block to arrive sums them (a fixed-shape
+//                   strided sum and warp tree), draws (or asserts) the
+//                   outcome and writes the scale.
 //   k_collapse      zero the rejected half, scale the kept half by
 //                   1/sqrt(p_outcome) in FP64 (RESET: move |1> onto |0>).
 //   k_expect        <psi|P_t|psi> partial sums in FP64 per (block, term),
@@ -58,6 +59,8 @@ __device__ __forceinline__ float2 scale_by(float2 a, double s) {
 __device__ __forceinline__ double2 scale_by(double2 a, double s) {
     return make_double2(a.x * s, a.y * s);
 }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
 __device__ __forceinline__ double2 to_d(double2 a) { return a; }
 
@@ -224,6 +227,56 @@ __device__ __forceinline__ void apply_dense_reg(T *tile, int m, const DevOp &op,
     }
 }
 
+// Monomial K-qubit op (K <= 2, see kMono1/kMono2): one complex multiply per
+// amplitude.  The product is formed with the same fused multiply-adds, in the
+// same order, as the nonzero term of apply_dense_reg's row sum (the zero terms
+// there add exact zeros), so both give the same values.
+template <int K, typename T, int NT>
+__device__ __forceinline__ void apply_mono(T *tile, int m, const DevOp &op, const T *mats) {
+    constexpr int D = 1 << K;
+    int sp[K];
+    unsigned off[D];
+    group_layout<K>(op, sp, off);
+    const T *M = mats + op.mat;
+    T mr[D];
+    unsigned offp[D];  // offset of the input each output row takes
+#pragma unroll
+    for (int r = 0; r < D; r++) {
+        const int c = (op.flags >> (2 * r)) & (D - 1);
+        mr[r] = M[r * D + c];
+        unsigned o = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) o |= ((unsigned)(c >> j) & 1u) << op.lq[j];
+        offp[r] = o;
+    }
+    constexpr int U = 4;
+    const unsigned G = 1u << (m - K);
+    for (unsigned g0 = threadIdx.x; g0 < G; g0 += U * NT) {
+        unsigned bb[U];
+        T x[U][D];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned g = g0 + u * NT;
+            unsigned b = g < G ? g : 0;
+#pragma unroll
+            for (int j = 0; j < K; j++) b = ins0(b, sp[j]);
+            bb[u] = b;
+#pragma unroll
+            for (int r = 0; r < D; r++) x[u][r] = tile[b + offp[r]];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (g0 + u * NT >= G) break;
+#pragma unroll
+            for (int r = 0; r < D; r++) {
+                T acc = czero(x[u][0]);
+                cmac(acc, mr[r], x[u][r]);
+                tile[bb[u] + off[r]] = acc;
+            }
+        }
+    }
+}
+
 // K >= 3: the matrix is read from shared memory (broadcast reads), so that its
 // 4^K entries are not all held in registers.  STAGE: copy it from global into
 // mbuf first; otherwise `mats` already points into shared memory.
@@ -274,14 +327,24 @@ __device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, con
     const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
     const bool odd = op.lq[4] & 1;
     const uint32_t zc = op.flags | ((uint32_t)op.pad << 16);
+    const bool scaled = op.lq[4] & 2;
     const T cs = mats[op.mat];
     const auto c = cs.x;
     const auto w = (__popc(zc & bid) & 1) ? -cs.y : cs.y;
     const unsigned Nt = 1u << m;
-    // (c, w) pair update: r = c a + u (odd ? i : 1) b
-    auto upd = [odd, c](T a, T b, decltype(c) u) {
+    // (c, w) pair update: r = c a + u (odd ? i : 1) b; scaled form (c = 1):
+    // r = a + u (odd ? i : 1) b, one fused multiply-add per component
+    auto upd = [odd, scaled, c](T a, T b, decltype(c) u) {
         T r;
-        if (odd) {
+        if (scaled) {
+            if (odd) {
+                r.x = fma_r(-u, b.y, a.x);
+                r.y = fma_r(u, b.x, a.y);
+            } else {
+                r.x = fma_r(u, b.x, a.x);
+                r.y = fma_r(u, b.y, a.y);
+            }
+        } else if (odd) {
             r.x = c * a.x - u * b.y;
             r.y = c * a.y + u * b.x;
         } else {
@@ -334,6 +397,8 @@ __device__ __forceinline__ void apply_op(T *tile, int m, const DevOp &op, const 
         case 7: apply_pauli<T, NT>(tile, m, op, mats, bid); break;
         case 1: apply_dense_reg<1, T, NT>(tile, m, op, mats); break;
         case 2: apply_dense_reg<2, T, NT>(tile, m, op, mats); break;
+        case kMono1: apply_mono<1, T, NT>(tile, m, op, mats); break;
+        case kMono2: apply_mono<2, T, NT>(tile, m, op, mats); break;
         case 3: if constexpr (KMAX >= 3) apply_dense_smem<3, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
         case 4: if constexpr (KMAX >= 4) apply_dense_smem<4, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
         case 5: if constexpr (KMAX >= 5) apply_dense_smem<5, T, NT, STAGE>(tile, m, op, mats, mbuf); break;
@@ -433,6 +498,30 @@ __device__ __forceinline__ void tile_pass_body(const TileArgs &a, const uint64_t
         apply_op<T, NT, KMAX, false>(tile, a.m, op, mats_s, nullptr, (uint32_t)bid);
         __syncthreads();
     }
+    if (a.wscale != 1.0) {  // times the cosines of the pass's scaled rotations
+        const R sc = (R)a.wscale;
+        if (vec) {
+            for (unsigned p = threadIdx.x; p < Nt / per; p += NT) {
+                const unsigned l = p * per;
+                T v[per];
+#pragma unroll
+                for (unsigned e = 0; e < per; e++) {
+                    v[e] = tile[l + e];
+                    v[e].x *= sc;
+                    v[e].y *= sc;
+                }
+                *reinterpret_cast<uint4 *>(st + (hi_off[l >> L] | (l & Lmask))) = *reinterpret_cast<const uint4 *>(v);
+            }
+        } else {
+            for (unsigned l = threadIdx.x; l < Nt; l += NT) {
+                T v = tile[l];
+                v.x *= sc;
+                v.y *= sc;
+                st[hi_off[l >> L] | (l & Lmask)] = v;
+            }
+        }
+        return;
+    }
     if (vec) {
         for (unsigned p = threadIdx.x; p < Nt / per; p += NT) {
             const unsigned l = p * per;
@@ -445,7 +534,7 @@ __device__ __forceinline__ void tile_pass_body(const TileArgs &a, const uint64_t
 }
 
 template <typename R, int NT, int KMAX>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass(TileArgs a) {
+__global__ void __launch_bounds__(NT, NT >= 512 || KMAX <= 2 ? 2 : 1) k_tile_pass(TileArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile_pass_body<R, NT, KMAX>(a, blockIdx.x, smem_raw);
 }
@@ -534,12 +623,151 @@ __device__ __forceinline__ void rot_reg_dispatch(float2 *a, unsigned sel, const 
     }
 }
 
-// The rotations of one segment, on this thread's registers: each takes the
-// half of its coefficient table that matches the thread's Z parity (RegRot).
+// ---- dense 1- and 2-qubit ops on register slots (RegDense) --
+// C1 on slot S: pairs (j, j | 2^S); each output summed with cmac from zero in
+// column order, as the shared-memory kernel does.
+template <int S>
+__device__ __forceinline__ void c1_reg(float2 *a, const float2 *M) {
+    const float4 r0 = *reinterpret_cast<const float4 *>(M), r1 = *reinterpret_cast<const float4 *>(M + 2);
+    const float2 m00 = make_float2(r0.x, r0.y), m01 = make_float2(r0.z, r0.w);
+    const float2 m10 = make_float2(r1.x, r1.y), m11 = make_float2(r1.z, r1.w);
+#pragma unroll
+    for (int p = 0; p < 16; p++) {
+        const int j = pair_lo(p, S), k = j | (1 << S);
+        const float2 x0 = a[j], x1 = a[k];
+        float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+        cmac(y0, m00, x0);
+        cmac(y0, m01, x1);
+        cmac(y1, m10, x0);
+        cmac(y1, m11, x1);
+        a[j] = y0;
+        a[k] = y1;
+    }
+}
+
+// C2 on slots S0 < S1 (bit 0 of the local index <-> S0): 8 groups of 4.
+template <int S0, int S1>
+__device__ __forceinline__ void c2_reg(float2 *a, const float2 *M) {
+    float2 m[16];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const float4 v = reinterpret_cast<const float4 *>(M)[i];
+        m[2 * i] = make_float2(v.x, v.y);
+        m[2 * i + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; g++) {
+        const int b = pair_lo(pair_lo(g, S0), S1);
+        const int idx[4] = {b, b | (1 << S0), b | (1 << S1), b | (1 << S0) | (1 << S1)};
+        float2 x[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) x[c] = a[idx[c]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 4; c++) cmac(acc, m[4 * r + c], x[c]);
+            a[idx[r]] = acc;
+        }
+    }
+}
+
+// One of x0..x3 by a runtime 2-bit column (selects, no local-memory indexing).
+__device__ __forceinline__ float2 pick4(unsigned c, float2 x0, float2 x1, float2 x2, float2 x3) {
+    const float2 lo = (c & 1u) ? x1 : x0, hi = (c & 1u) ? x3 : x2;
+    return (c & 2u) ? hi : lo;
+}
+
+// Monomial C1 on slot S: out_r = M[r][perm_r] x_{perm_r}.
+template <int S>
+__device__ __forceinline__ void mono1_reg(float2 *a, const float2 *M, unsigned perm) {
+    const unsigned c0 = perm & 1u, c1 = (perm >> 2) & 1u;
+    const float2 m0 = M[c0], m1 = M[2 + c1];
+#pragma unroll
+    for (int p = 0; p < 16; p++) {
+        const int j = pair_lo(p, S), k = j | (1 << S);
+        const float2 x0 = a[j], x1 = a[k];
+        float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+        cmac(y0, m0, c0 ? x1 : x0);
+        cmac(y1, m1, c1 ? x1 : x0);
+        a[j] = y0;
+        a[k] = y1;
+    }
+}
+
+// Monomial C2 on slots S0 < S1.
+template <int S0, int S1>
+__device__ __forceinline__ void mono2_reg(float2 *a, const float2 *M, unsigned perm) {
+    unsigned c[4];
+    float2 m[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        c[r] = (perm >> (2 * r)) & 3u;
+        m[r] = M[4 * r + c[r]];
+    }
+#pragma unroll
+    for (int g = 0; g < 8; g++) {
+        const int b = pair_lo(pair_lo(g, S0), S1);
+        const int idx[4] = {b, b | (1 << S0), b | (1 << S1), b | (1 << S0) | (1 << S1)};
+        const float2 x0 = a[idx[0]], x1 = a[idx[1]], x2 = a[idx[2]], x3 = a[idx[3]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            float2 acc = make_float2(0.f, 0.f);
+            cmac(acc, m[r], pick4(c[r], x0, x1, x2, x3));
+            a[idx[r]] = acc;
+        }
+    }
+}
+
+__device__ __forceinline__ void dense_reg_dispatch(float2 *a, unsigned sel, unsigned perm, const float2 *M) {
+    switch (sel) {
+        case 0: c1_reg<0>(a, M); break;
+        case 1: c1_reg<1>(a, M); break;
+        case 2: c1_reg<2>(a, M); break;
+        case 3: c1_reg<3>(a, M); break;
+        case 4: c1_reg<4>(a, M); break;
+        case 5: c2_reg<0, 1>(a, M); break;
+        case 6: c2_reg<0, 2>(a, M); break;
+        case 7: c2_reg<0, 3>(a, M); break;
+        case 8: c2_reg<0, 4>(a, M); break;
+        case 9: c2_reg<1, 2>(a, M); break;
+        case 10: c2_reg<1, 3>(a, M); break;
+        case 11: c2_reg<1, 4>(a, M); break;
+        case 12: c2_reg<2, 3>(a, M); break;
+        case 13: c2_reg<2, 4>(a, M); break;
+        case 14: c2_reg<3, 4>(a, M); break;
+        case 15: mono1_reg<0>(a, M, perm); break;
+        case 16: mono1_reg<1>(a, M, perm); break;
+        case 17: mono1_reg<2>(a, M, perm); break;
+        case 18: mono1_reg<3>(a, M, perm); break;
+        case 19: mono1_reg<4>(a, M, perm); break;
+        case 20: mono2_reg<0, 1>(a, M, perm); break;
+        case 21: mono2_reg<0, 2>(a, M, perm); break;
+        case 22: mono2_reg<0, 3>(a, M, perm); break;
+        case 23: mono2_reg<0, 4>(a, M, perm); break;
+        case 24: mono2_reg<1, 2>(a, M, perm); break;
+        case 25: mono2_reg<1, 3>(a, M, perm); break;
+        case 26: mono2_reg<1, 4>(a, M, perm); break;
+        case 27: mono2_reg<2, 3>(a, M, perm); break;
+        case 28: mono2_reg<2, 4>(a, M, perm); break;
+        case 29: mono2_reg<3, 4>(a, M, perm); break;
+        default: break;
+    }
+}
+
+// The ops of one segment, on this thread's registers: each rotation takes the
+// half of its coefficient table that matches the thread's Z parity (RegRot);
+// with DENSE, a RegDense op applies its matrix to its slots.
+template <bool DENSE>
 __device__ __forceinline__ void seg_rotations(float2 *reg, const RegRot *ops, uint32_t count, uint32_t tb,
                                               uint32_t bid, const float *coef) {
     for (uint32_t k = 0; k < count; k++) {
         const RegRot op = ops[k];
+        if (DENSE && op.k == kDenseReg) {
+            const RegDense d = *reinterpret_cast<const RegDense *>(ops + k);
+            dense_reg_dispatch(reg, d.sel, d.perm, reinterpret_cast<const float2 *>(coef + d.tab));
+            continue;
+        }
         const uint32_t pt = (__popc(tb & op.zt) ^ __popc(op.zc & bid)) & 1u;
         if (op.sel >> 1) {
             rot_reg_dispatch(reg, op.sel, reinterpret_cast<const float4 *>(coef + op.tab + 16 * pt));
@@ -575,7 +803,7 @@ __device__ __forceinline__ void seg_load_smem(float2 *reg, uint32_t addr, const 
     }
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool DENSE>
 __global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
@@ -632,7 +860,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
             } else {
                 seg_load_smem(reg, sa, sd);
             }
-            seg_rotations(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
+            seg_rotations<DENSE>(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
                           reinterpret_cast<const float *>(mats_s));
             if (last) {
                 uint32_t g = x0;
@@ -648,7 +876,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
         } else {
             seg_load_smem(reg, sa, sd);
             __syncthreads();  // all reads of this layout before the next one is written
-            seg_rotations(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
+            seg_rotations<DENSE>(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
                           reinterpret_cast<const float *>(mats_s));
         }
         sa_prev = sa;
@@ -883,7 +1111,7 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 8 : NT <= 128 ? 4 : 2)
                 seg_load_smem(reg, sa, sd);
                 if (!last) __syncthreads();
             }
-            seg_rotations(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
+            seg_rotations<false>(reg, reinterpret_cast<const RegRot *>(ops_s) + i + 1, nseg, tb, bid,
                           reinterpret_cast<const float *>(mats_s));
             if (last) {
                 uint32_t gd[5];
@@ -913,7 +1141,7 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 8 : NT <= 128 ? 4 : 2)
 // blocks [cta_first_j, cta_first_{j+1}); each block finds its state's pass by
 // binary search and runs it on tile (blockIdx.x - cta_first_j).
 template <typename R, int NT, int KMAX>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1) k_tile_pass_multi(const TileArgs *descs,
+__global__ void __launch_bounds__(NT, NT >= 512 || KMAX <= 2 ? 2 : 1) k_tile_pass_multi(const TileArgs *descs,
                                                                             int n_desc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileArgs d;
@@ -1052,7 +1280,6 @@ __global__ void __launch_bounds__(kRedThreads) k_prob(const void *state, int n, 
                                                       double *partials, MeasCtl *ctl, MeasRec *log) {
     using T = typename V2<R>::T;
     __shared__ double red[2 * kRedThreads / 32];
-    __shared__ double part[2 * 1024];
     __shared__ int last;
     if (ctl->status) return;
     const T *st = reinterpret_cast<const T *>(state);
@@ -1077,17 +1304,16 @@ __global__ void __launch_bounds__(kRedThreads) k_prob(const void *state, int n, 
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // the block partials in a fixed shape: thread t sums blocks t, t + 256, ...
+    // in order, then the warp-shuffle / warp-order tree of block_sum2, so the
+    // result depends only on the grid size (no serial chain over all blocks)
+    double x = 0, y = 0;
     for (unsigned b = threadIdx.x; b < gridDim.x; b += kRedThreads) {
-        part[2 * b] = __ldcg(partials + 2 * b);
-        part[2 * b + 1] = __ldcg(partials + 2 * b + 1);
+        x += __ldcg(partials + 2 * b);
+        y += __ldcg(partials + 2 * b + 1);
     }
-    __syncthreads();
+    block_sum2<kRedThreads>(x, y, red);
     if (threadIdx.x == 0) {
-        double x = 0, y = 0;
-        for (unsigned b = 0; b < gridDim.x; b++) {
-            x += part[2 * b];
-            y += part[2 * b + 1];
-        }
         ctl->arrive = 0;
         ctl->p0 = x;
         ctl->p1 = y;
@@ -1225,9 +1451,12 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_tile_pass<double, 512, 2>));
     QSIM_ATTR((k_tile_pass<float, 256, 5>));
     QSIM_ATTR((k_tile_pass<double, 256, 5>));
-    QSIM_ATTR((k_rot_pass<128, 4>));
-    QSIM_ATTR((k_rot_pass<256, 2>));
-    QSIM_ATTR((k_rot_pass<512, 1>));
+    QSIM_ATTR((k_rot_pass<128, 4, false>));
+    QSIM_ATTR((k_rot_pass<256, 2, false>));
+    QSIM_ATTR((k_rot_pass<512, 1, false>));
+    QSIM_ATTR((k_rot_pass<128, 4, true>));
+    QSIM_ATTR((k_rot_pass<256, 2, true>));
+    QSIM_ATTR((k_rot_pass<512, 1, true>));
     QSIM_ATTR(k_rot_pipe<64>);
     QSIM_ATTR(k_rot_pipe<128>);
     QSIM_ATTR(k_rot_pipe<256>);
@@ -1288,6 +1517,7 @@ bool make_tile_args(int dtype, void *state, int n, int m, uint64_t pivots, const
         if (ok) break;
     }
     a.L = L;
+    a.wscale = 1.0;
     return true;
 }
 
@@ -1312,12 +1542,13 @@ bool generic_tile_ok(const TileArgs &a) { return (1 << (a.m - a.L)) <= kMaxHi; }
 
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
                              uint64_t pivots, const uint64_t *basis, const DevOp *ops, uint32_t n_ops,
-                             const void *mats, uint32_t mat_first, uint32_t mat_count,
+                             const void *mats, uint32_t mat_first, uint32_t mat_count, double wscale,
                              const MeasCtl *ctl, cudaStream_t s) {
     TileArgs a;
     if (!make_tile_args(dtype, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a) ||
         !generic_tile_ok(a))
         return cudaErrorInvalidValue;
+    a.wscale = wscale;
     const unsigned grid = 1u << (n - m);
     const size_t smem = tile_smem_bytes(dtype, m);
     if (kmax > 2) {
@@ -1334,16 +1565,22 @@ cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int 
 
 cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
                             const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
-                            uint32_t mat_count, float scale, const MeasCtl *ctl, cudaStream_t s) {
+                            uint32_t mat_count, float scale, bool dense, const MeasCtl *ctl, cudaStream_t s) {
     if (m < 10 || m > 14 || n > 32) return cudaErrorInvalidValue;
     TileArgs a;
     if (!make_tile_args(0, state, n, m, pivots, basis, ops, n_ops, mats, mat_first, mat_count, ctl, &a))
         return cudaErrorInvalidValue;
     a.scale = scale;
     const unsigned grid = 1u << (n - m), threads = 1u << (m - 5);
-    if (m == 12) return launch_dependent(k_rot_pass<128, 4>, grid, threads, tile_smem_bytes(0, m), s, a);
-    if (m <= 13) return launch_dependent(k_rot_pass<256, 2>, grid, threads, tile_smem_bytes(0, m), s, a);
-    return launch_dependent(k_rot_pass<512, 1>, grid, threads, tile_smem_bytes(0, m), s, a);
+    const size_t smem = tile_smem_bytes(0, m);
+    if (dense) {
+        if (m == 12) return launch_dependent(k_rot_pass<128, 4, true>, grid, threads, smem, s, a);
+        if (m <= 13) return launch_dependent(k_rot_pass<256, 2, true>, grid, threads, smem, s, a);
+        return launch_dependent(k_rot_pass<512, 1, true>, grid, threads, smem, s, a);
+    }
+    if (m == 12) return launch_dependent(k_rot_pass<128, 4, false>, grid, threads, smem, s, a);
+    if (m <= 13) return launch_dependent(k_rot_pass<256, 2, false>, grid, threads, smem, s, a);
+    return launch_dependent(k_rot_pass<512, 1, false>, grid, threads, smem, s, a);
 }
 
 cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,

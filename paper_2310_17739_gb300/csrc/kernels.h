@@ -17,6 +17,9 @@ namespace qsim {
 // factor is i W rather than W), Z parity mask over the tile origin's bits in
 // flags | pad << 16, coefficient (cos theta, W) at mats[mat]:
 //   a'_j = cos a_j + W (odd ? i : 1) (-1)^{parity(k & z) ^ parity(zc & tile)} a_k,  k = j ^ x.
+// lq[4] bit 1 = scaled: the coefficient is (cos theta, t = W / cos theta) and
+// the op computes a'_j = a_j + t (odd ? i : 1) (...) a_k, the missing cosine
+// being part of the pass's write-back factor (TileArgs::wscale).
 // Inside a register segment a rotation is a RegRot instead.
 struct DevOp {
     uint8_t k;
@@ -108,6 +111,8 @@ struct TileArgs {
     uint32_t pad;
     float scale;         // register-segment passes: factor applied when the tile is written back
     uint32_t pad2;
+    double wscale;       // generic passes: factor applied when the tile is written back (the
+                         // product of the cosines of its scaled rotations; 1 = none)
     uint64_t bv[16];     // tile basis: tile bit j <-> amplitude-index XOR bv[j] (m entries)
     uint8_t ntq[48];     // non-pivot qubits, ascending (n - m entries): the tile origin's bits
 };
@@ -120,13 +125,15 @@ bool make_tile_args(int dtype, void *state, int n, int m, uint64_t pivots, const
 // tile: it tabulates the offsets of the 2^(m-L) tile rows in a fixed shared
 // array of 1024 entries.
 bool generic_tile_ok(const TileArgs &a);
-// A complex64 pass of rotations laid out in register segments (see
-// kSegMarker): 2^(m-5) threads, 32 amplitudes each; 10 <= m <= 14, n <= 32.
-// Its rotations carry (cos, t = W / cos) and run as a' = a + t (...) with the
-// cosines' product `scale` applied when the tile is written back.
+// A complex64 pass laid out in register segments (see kSegMarker): 2^(m-5)
+// threads, 32 amplitudes each; 10 <= m <= 14, n <= 32.  Its rotations carry
+// (cos, t = W / cos) and run as a' = a + t (...) with the cosines' product
+// `scale` applied when the tile is written back.  dense: the pass also holds
+// RegDense ops (a separate build of the kernel; rotation-only passes keep the
+// build without them).
 cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
                             const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
-                            uint32_t mat_count, float scale, const MeasCtl *ctl, cudaStream_t s);
+                            uint32_t mat_count, float scale, bool dense, const MeasCtl *ctl, cudaStream_t s);
 // The same pass with resident blocks taking tiles from the device counter
 // *ctr (numbers base .. base + 2^(n-m) - 1 are this pass's tiles), each
 // prefetching its next tile while it computes the current one.  A launch
@@ -139,6 +146,14 @@ cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const ui
 // Op-size marker of a register segment: lq[0..4] = the 5 tile positions held
 // in registers, flags = number of rotations that follow in the segment.
 constexpr uint8_t kSegMarker = 8;
+// Monomial 1- and 2-qubit ops (at most one nonzero entry per row: diagonal
+// gates, permutations such as X, CX, SWAP, and their products with phases):
+// as a dense op of k = 1 / 2 qubits (lq, mat), but only the entry of each row
+// r in column perm[r] = (flags >> 2r) & 3 is used (a row without a nonzero
+// names column 0, whose entry is then zero):
+//   out_r = M[r][perm[r]] * in_{perm[r]}.
+constexpr uint8_t kMono1 = 9;
+constexpr uint8_t kMono2 = 10;
 // A rotation inside a register segment (the 16 bytes of a DevOp slot).  sel =
 // xr << 1 | odd, xr its X mask over the segment's 5 register slots; zt its
 // tile-local Z mask; zc as in DevOp; tab = offset (in floats, a multiple of
@@ -161,6 +176,27 @@ struct RegRot {
     uint32_t pad;
 };
 static_assert(sizeof(RegRot) == sizeof(DevOp), "RegRot layout");
+// A dense 1- or 2-qubit op inside a register segment (the 16 bytes of a
+// DevOp slot), k = kDenseReg.  sel names the kind and the register slots:
+//   0..4    C1 on slot s = sel
+//   5..14   C2 on the slot pair number sel - 5 of (0,1) (0,2) (0,3) (0,4) (1,2)
+//           (1,3) (1,4) (2,3) (2,4) (3,4)
+//   15..19  monomial C1 on slot sel - 15
+//   20..29  monomial C2 on the slot pair number sel - 20
+// Its 2^k x 2^k complex matrix (row-major, bit 0 of the local index <-> the
+// lower slot) is at float offset tab (a multiple of 4) of the pass's
+// coefficient slice; a monomial op uses only the entry in column
+// perm[r] = (perm >> 2r) & 3 of each row r (as kMono1 / kMono2).
+constexpr uint8_t kDenseReg = 11;
+struct RegDense {
+    uint8_t k;  // kDenseReg
+    uint8_t sel;
+    uint16_t perm;
+    uint32_t tab;
+    uint32_t pad0;
+    uint32_t pad1;
+};
+static_assert(sizeof(RegDense) == sizeof(DevOp), "RegDense layout");
 // Several states' passes in one launch: descs[0..n_desc) in device memory with
 // increasing cta_first; total_ctas blocks; max_m the largest tile among them.
 cudaError_t launch_tile_pass_multi(int dtype, int threads, int kmax, const TileArgs *d_descs,
@@ -177,7 +213,7 @@ size_t tile_smem_bytes(int dtype, int m);
 // op (qubits); <= 2 selects the register-lean build without k >= 3 paths.
 cudaError_t launch_tile_pass(int dtype, int threads, int kmax, void *state, int n, int m,
                              uint64_t pivots, const uint64_t *basis, const DevOp *ops, uint32_t n_ops,
-                             const void *mats, uint32_t mat_first, uint32_t mat_count,
+                             const void *mats, uint32_t mat_first, uint32_t mat_count, double wscale,
                              const MeasCtl *ctl, cudaStream_t s);
 // Resident whole-state interpreter; kmax as for launch_tile_pass.  The batch
 // form runs one block per instance, shared memory sized for max_n qubits.

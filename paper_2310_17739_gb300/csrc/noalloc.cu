@@ -57,6 +57,24 @@ extern "C" QSIM_API qsim_status qsim_prob_noalloc(const void *d_state, int n_qub
         cudaGetLastError();
         return QSIM_E_CUDA;
     }
+    // The scratch address below is the current device's copy of the array, so
+    // the state and the stream must belong to that device too.
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, d_state) != cudaSuccess) {
+        cudaGetLastError();
+        return QSIM_E_INVAL;
+    }
+    if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
+        (pa.type == cudaMemoryTypeDevice && pa.device != dev))
+        return QSIM_E_INVAL;
+    if (stream) {
+        int sdev = -1;
+        if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return QSIM_E_INVAL;
+        }
+        if (sdev != dev) return QSIM_E_INVAL;
+    }
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);

@@ -6,8 +6,9 @@
 // files use: qreg / creg declarations, the qelib1 gate set (applied to single
 // qubits or broadcast over whole registers), parameter expressions (pi,
 // + - * / ^, unary minus, sin cos tan exp ln sqrt), user `gate` definitions
-// (expanded like macros), measure / reset / barrier.  ccx and cswap are
-// decomposed into 1- and 2-qubit gates; sx / sxdg become C1 records.  Global
+// (expanded like macros), measure / reset / barrier.  ccx, cswap, rccx and
+// rc3x are decomposed into 1- and 2-qubit gates, c3x, c4x and c3sqrtx into
+// controlled-X^t C2 records; sx / sxdg become C1 records.  Global
 // phases follow the library's gate definitions (RZ(t) = exp(-i t Z/2),
 // U3 as the standard three-angle matrix), as Qiskit's gates do.
 #include <cctype>
@@ -457,6 +458,65 @@ class Parser {
         gates.push_back(g);
     }
 
+    // X^t = ((1 + e^{i pi t}) I + (1 - e^{i pi t}) X) / 2 (principal power: t = 1
+    // is X, t = 1/2 the sqrt(X) of `sx`), as a 2x2 complex matrix (re, im).
+    static void xpow(double t, double *m8) {
+        const double kPi = 3.14159265358979323846;
+        // e^{i pi t}, exact where it has an exact value (X and sqrt(X) stay exact)
+        double cr = std::cos(kPi * t), ci = std::sin(kPi * t);
+        if (t == 1.0) cr = -1.0, ci = 0.0;
+        if (t == 0.5 || t == -0.5) cr = 0.0, ci = t > 0 ? 1.0 : -1.0;
+        const double d[2] = {(1 + cr) / 2, ci / 2}, o[2] = {(1 - cr) / 2, -ci / 2};
+        m8[0] = d[0]; m8[1] = d[1]; m8[2] = o[0]; m8[3] = o[1];
+        m8[4] = o[0]; m8[5] = o[1]; m8[6] = d[0]; m8[7] = d[1];
+    }
+    // Controlled-U on (control c, target t) as a C2 record: |0><0| (x) I + |1><1| (x) U
+    // in the local basis l = b_c + 2 b_t.
+    void push_controlled(int c, int t, const double *u8) {
+        double m[32] = {0};
+        auto set = [&](int r, int col, double re, double im) {
+            m[2 * (4 * r + col)] = re;
+            m[2 * (4 * r + col) + 1] = im;
+        };
+        set(0, 0, 1, 0);
+        set(2, 2, 1, 0);
+        for (int i = 0; i < 2; i++)      // target bit (row) with the control bit 1
+            for (int j = 0; j < 2; j++)  // target bit (column)
+                set(1 + 2 * i, 1 + 2 * j, u8[2 * (2 * i + j)], u8[2 * (2 * i + j) + 1]);
+        qsim_gate g;
+        std::memset(&g, 0, sizeof(g));
+        g.op = QSIM_OP_C2;
+        g.q0 = (uint32_t)c;
+        g.q1 = (uint32_t)t;
+        g.mat = (uint32_t)mats.size();
+        mats.insert(mats.end(), m, m + 32);
+        gates.push_back(g);
+    }
+    // X^t on `target` controlled by every qubit of `ctl`, exactly (no relative
+    // phase), by the recursion of Barenco et al., Phys. Rev. A 52, 3457 (1995),
+    // Lemma 7.5: with V = X^{t/2} and c the last control,
+    //   C^k(X^t) = C^{k-1}(V) . C^{k-1}(X)[-> c] . C_c(V^dagger) . C^{k-1}(X)[-> c] . C_c(V)
+    // (rightmost first): the two inner gates flip c only when the other controls
+    // are all 1, so the target receives V V = X^t exactly when every control is 1
+    // and V V^dagger = I or nothing otherwise.
+    void multi_controlled_xpow(const std::vector<int> &ctl, int target, double t) {
+        double u[8];
+        if (ctl.size() == 1) {
+            xpow(t, u);
+            push_controlled(ctl[0], target, u);
+            return;
+        }
+        const int c = ctl.back();
+        const std::vector<int> rest(ctl.begin(), ctl.end() - 1);
+        xpow(t / 2, u);
+        push_controlled(c, target, u);
+        multi_controlled_xpow(rest, c, 1.0);
+        xpow(-t / 2, u);
+        push_controlled(c, target, u);
+        multi_controlled_xpow(rest, c, 1.0);
+        multi_controlled_xpow(rest, target, t / 2);
+    }
+
     // One gate on resolved qubits: a built-in of qelib1, or a user definition.
     void apply(const std::string &name, const std::vector<double> &p, const std::vector<int> &q, int line) {
         struct B {
@@ -521,6 +581,57 @@ class Parser {
             push(QSIM_OP_CX, q[2], q[1], 0, 0, 0);
             apply("ccx", {}, {q[0], q[1], q[2]}, line);
             push(QSIM_OP_CX, q[2], q[1], 0, 0, 0);
+            return;
+        }
+        if (name == "c3x" || name == "c4x" || name == "c3sqrtx") {
+            // exact multi-controlled X^t (t = 1, or 1/2 for sqrt(X)), phase included
+            const size_t nc = name == "c4x" ? 4 : 3;
+            check(nc + 1, 0);
+            const std::vector<int> ctl(q.begin(), q.begin() + nc);
+            multi_controlled_xpow(ctl, q[nc], name == "c3sqrtx" ? 0.5 : 1.0);
+            return;
+        }
+        if (name == "rccx") {
+            // relative-phase Toffoli (Margolus form in Clifford+T; Maslov, Phys. Rev. A
+            // 93, 022311 (2016)): Toffoli followed by the phases -i on |a b c> = |110>,
+            // +i on |111> and -1 on |101> (a, b controls, c target)
+            check(3, 0);
+            const int a = q[0], b = q[1], c = q[2];
+            push(QSIM_OP_H, c, 0, 0, 0, 0);
+            push(QSIM_OP_T, c, 0, 0, 0, 0);
+            push(QSIM_OP_CX, b, c, 0, 0, 0);
+            push(QSIM_OP_TDG, c, 0, 0, 0, 0);
+            push(QSIM_OP_CX, a, c, 0, 0, 0);
+            push(QSIM_OP_T, c, 0, 0, 0, 0);
+            push(QSIM_OP_CX, b, c, 0, 0, 0);
+            push(QSIM_OP_TDG, c, 0, 0, 0, 0);
+            push(QSIM_OP_H, c, 0, 0, 0, 0);
+            return;
+        }
+        if (name == "rc3x") {
+            // relative-phase 3-controlled X (Maslov 2016, Clifford+T): C3X followed by
+            // the phases +i on |a b c d> = |1100>, -i on |1101> and -1 on |1111>
+            // (a, b, c controls, d target)
+            check(4, 0);
+            const int a = q[0], b = q[1], c = q[2], d = q[3];
+            push(QSIM_OP_H, d, 0, 0, 0, 0);
+            push(QSIM_OP_T, d, 0, 0, 0, 0);
+            push(QSIM_OP_CX, c, d, 0, 0, 0);
+            push(QSIM_OP_TDG, d, 0, 0, 0, 0);
+            push(QSIM_OP_H, d, 0, 0, 0, 0);
+            push(QSIM_OP_CX, a, d, 0, 0, 0);
+            push(QSIM_OP_T, d, 0, 0, 0, 0);
+            push(QSIM_OP_CX, b, d, 0, 0, 0);
+            push(QSIM_OP_TDG, d, 0, 0, 0, 0);
+            push(QSIM_OP_CX, a, d, 0, 0, 0);
+            push(QSIM_OP_T, d, 0, 0, 0, 0);
+            push(QSIM_OP_CX, b, d, 0, 0, 0);
+            push(QSIM_OP_TDG, d, 0, 0, 0, 0);
+            push(QSIM_OP_H, d, 0, 0, 0, 0);
+            push(QSIM_OP_T, d, 0, 0, 0, 0);
+            push(QSIM_OP_CX, c, d, 0, 0, 0);
+            push(QSIM_OP_TDG, d, 0, 0, 0, 0);
+            push(QSIM_OP_H, d, 0, 0, 0, 0);
             return;
         }
         auto d = defs_.find(name);

@@ -27,13 +27,13 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 C64, C128 = 0, 1
 PAULI_K = 7  # op-size marker of a Pauli rotation in the compiled op list
-OK, E_INVAL, E_OOM, E_CUDA, E_ZEROPROB, E_TIMEOUT, E_STATE = range(7)
+OK, E_INVAL, E_OOM, E_CUDA, E_ZEROPROB, E_TIMEOUT, E_STATE, E_CANCELED = range(8)
 MEAS_ASSERT = 1
 _vp, _sz, _u64, _i32, _dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
 
 
 class QsimConfig(ctypes.Structure):
-    _fields_ = [("fusion", ctypes.c_int32), ("k_max", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
+    _fields_ = [("struct_size", ctypes.c_uint32), ("fusion", ctypes.c_int32), ("k_max", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("chunk_gates", ctypes.c_int32),
                 ("lookahead", ctypes.c_int32), ("compile_threads", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("graphs", ctypes.c_int32), ("forced_low", ctypes.c_int32)]
@@ -78,10 +78,14 @@ _SIGS = {
     "qsim_reset_state": ([_vp], _i32),
     "qsim_state_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)], _i32),
     "qsim_sync": ([_vp], _i32),
+    "qsim_sync_timeout": ([_vp, _dbl], _i32),
+    "qsim_config_init": ([ctypes.POINTER(QsimConfig)], None),
+    "qsim_server_cancel": ([_vp, _u64], _i32),
     "qsim_batch_create": ([_i32, _vp, _i32, _vp, ALLOC_FN, FREE_FN, _vp, ctypes.POINTER(_vp)], _i32),
     "qsim_batch_destroy": ([_vp], _i32),
     "qsim_batch_set_config": ([_vp, ctypes.POINTER(QsimConfig)], _i32),
     "qsim_batch_set_seeds": ([_vp, _vp], _i32),
+    "qsim_batch_set_instance_config": ([_vp, _i32, ctypes.POINTER(QsimConfig)], _i32),
     "qsim_batch_compile": ([_vp, _i32, _vp, _sz, _vp, _sz], _i32),
     "qsim_batch_compile_many": ([_vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32], _i32),
     "qsim_batch_run": ([_vp], _i32),
@@ -148,8 +152,8 @@ def _mats(m):
 
 def make_config(fusion=1, k_max=2, tile_bits=0, threads=0, chunk_gates=0, lookahead=0,
                 compile_threads=0, persistent=0, graphs=0, forced_low=0) -> QsimConfig:
-    return QsimConfig(fusion, k_max, tile_bits, threads, chunk_gates, lookahead, compile_threads, persistent,
-                      graphs, forced_low)
+    return QsimConfig(ctypes.sizeof(QsimConfig), fusion, k_max, tile_bits, threads, chunk_gates, lookahead,
+                      compile_threads, persistent, graphs, forced_low)
 
 
 # ----------------------------------------------------------- torch plumbing --
@@ -327,6 +331,10 @@ class Sim:
     def sync(self):
         return _lib.qsim_sync(self.h)
 
+    def sync_timeout(self, seconds: float):
+        """qsim_sync with a bounded wait: E_TIMEOUT if the work is still running."""
+        return _lib.qsim_sync_timeout(self.h, float(seconds))
+
     # -- sampled kernel timing
     def sample(self, shots: int, seed: int = 0, mask: int | None = None) -> np.ndarray:
         """Final-state shots without collapse (see qsim_sample): packed bits of `mask`
@@ -389,6 +397,10 @@ class Batch:
 
     def __len__(self):
         return len(self.n)
+
+    def set_instance_config(self, index: int, **config):
+        """Configuration of one instance (applies to its next compile)."""
+        _check(_lib.qsim_batch_set_instance_config(self.h, index, ctypes.byref(make_config(**config))))
 
     def compile(self, index: int, gates, mats=None):
         g = _gates(gates)
@@ -492,6 +504,10 @@ class Server:
                                 t_admit=r.t_admit, t_done=r.t_done))
             if k.value < 256:
                 return out
+
+    def cancel(self, rid: int) -> int:
+        """Cancel a request that has not been admitted (status of the call)."""
+        return _lib.qsim_server_cancel(self.h, rid)
 
     def counts(self) -> dict:
         v = [ctypes.c_uint64() for _ in range(5)]

@@ -505,3 +505,34 @@ def test_default_tile_size_rule(n):
     assert tiles and set(tiles) == {min(14, max(10, n - 8))}
     tiles = [bin(p[0]).count("1") for p in qs.schedule(n, c.gates, dtype=qs.C128, fusion=2) if p[0]]
     assert tiles and set(tiles) == {min(13, max(10, n - 8))}
+
+
+def test_config_struct_size_and_ranges_are_checked():
+    """Every call that reads a qsim_config refuses one whose struct_size is not
+    this library's sizeof(qsim_config) (a caller built against another layout)
+    and fields out of range; qsim_config_init gives the documented defaults."""
+    import ctypes
+    c = qs.QsimConfig()
+    qs.lib().qsim_config_init(ctypes.byref(c))
+    assert c.struct_size == ctypes.sizeof(qs.QsimConfig) == 44
+    assert (c.fusion, c.k_max, c.tile_bits, c.forced_low, c.graphs) == (1, 2, 0, 0, 0)
+    g = W.records([(OP["H"], 0, 0, 0, 0, 0), (OP["CX"], 0, 1, 0, 0, 0)])
+    nops, nmd = ctypes.c_size_t(), ctypes.c_size_t()
+
+    def fuse_status(cfg, dtype=qs.C64):
+        return qs.lib().qsim_fuse(4, dtype, qs._ptr(g), g.size, None, 0, ctypes.byref(cfg), None, None, None, 0,
+                                  None, 0, ctypes.byref(nops), ctypes.byref(nmd))
+    # capacity 0 on a valid config: E_INVAL only for "capacity too small", with sizes set
+    assert fuse_status(c) == qs.E_INVAL and nops.value > 0
+    bad = qs.make_config()
+    bad.struct_size = 40                 # an older 10-field layout
+    nops.value = 0
+    assert fuse_status(bad) == qs.E_INVAL and nops.value == 0
+    assert "struct_size" in qs.lib().qsim_last_error(None).decode()
+    for kw, dtype in ((dict(forced_low=5), qs.C64), (dict(forced_low=4), qs.C128), (dict(fusion=3), qs.C64),
+                      (dict(k_max=6), qs.C64), (dict(tile_bits=14), qs.C128), (dict(graphs=3), qs.C64)):
+        nops.value = 0
+        assert fuse_status(qs.make_config(**kw), dtype) == qs.E_INVAL and nops.value == 0, kw
+    nops.value = 0
+    assert fuse_status(qs.make_config(forced_low=4), qs.C64) == qs.E_INVAL and nops.value > 0
+    assert qs.lib().qsim_status_string(qs.E_CANCELED).decode() == "request cancelled"

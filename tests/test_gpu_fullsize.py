@@ -1,6 +1,10 @@
-"""Full-size checks in the benchmark's launch configuration, where the CPU
-oracle cannot run the whole circuit: properties that hold at any size, and
-oracle parity on a prefix."""
+"""Full-size checks in the benchmark's launch configuration: the 16-qubit
+1e6-gate circuit against the whole oracle run; where the oracle cannot run the
+whole circuit (21 qubits, 1.15e8 gates), the two precisions against each
+other and properties that hold at any size; states above L2 size (24 qubits,
+oracle parity) and above 2^32 amplitudes (33 qubits, closed forms)."""
+import threading
+
 import numpy as np
 import pytest
 
@@ -71,3 +75,104 @@ def test_mid_config_full_size():
     out, prob = sim.outcomes()
     assert np.array_equal(out, r.outcomes)
     assert np.abs(sim.state() - ref).max() <= 1e-10
+
+
+def test_large_circuit_with_its_measurements_in_both_precisions():
+    """The benchmark's 21-qubit circuit of 1.15e8 gates with its 8 mid-circuit
+    measurements, complex64 in the benchmark's configuration and complex128
+    (the paper's arithmetic): the same 8 outcomes and final states within
+    infidelity 1e-5 (no oracle can run this circuit; the complex128 run is the
+    reference the complex64 result is stated against)."""
+    c = W.config_large(n_meas=8)
+    runs = {}
+    for dt, cfg in (("c64", BENCH_CFG), ("c128", dict(fusion=2))):
+        sim = qs.Sim(21, dt, seed=1003, config=cfg)
+        sim.apply(c.gates)
+        assert sim.sync() == 0
+        runs[dt] = (sim.state(), sim.outcomes())
+        sim.close()
+    (s64, (o64, p64)), (s128, (o128, p128)) = runs["c64"], runs["c128"]
+    assert len(o128) == 8 and np.array_equal(o64, o128)
+    assert np.abs(p64 - p128).max() <= 1e-5
+    assert abs(float(np.vdot(s128, s128).real) - 1.0) <= 1e-9
+    assert 1 - H.fidelity(s128, s64) <= 1e-5
+
+
+def test_mid_config_against_the_whole_oracle_run():
+    """16 qubits, 1e6 gates, 64 mid-circuit measurements (draws philox(1002, k)):
+    the oracle runs the whole circuit (in a thread: the C call releases the
+    interpreter lock) while the GPU runs it in complex128 and complex64.
+    Outcomes bit-exact, complex128 amplitudes within 1e-10, complex64 within
+    infidelity 1e-5."""
+    c = W.config_mid()
+    ref = oracle.basis_state(16)
+    box = {}
+    th = threading.Thread(target=lambda: box.update(r=oracle.run(ref, 16, c.gates, seed=1002)))
+    th.start()
+    runs = {}
+    for dt in ("c128", "c64"):
+        sim = qs.Sim(16, dt, seed=1002, config=dict(fusion=2))
+        sim.apply(c.gates)
+        assert sim.sync() == 0
+        runs[dt] = (sim.state(), sim.outcomes())
+        sim.close()
+    th.join()
+    r = box["r"]
+    assert r.status == 0 and len(r.outcomes) == 64
+    (s128, (o128, p128)), (s64, (o64, p64)) = runs["c128"], runs["c64"]
+    assert np.array_equal(o128, r.outcomes) and np.array_equal(o64, r.outcomes)
+    assert np.abs(p128 - r.probs).max() <= 1e-10
+    assert np.abs(s128 - ref).max() <= 1e-10
+    assert 1 - H.fidelity(ref, s64) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,cfg", [("c64", BENCH_CFG), ("c64", dict(fusion=1)), ("c128", dict(fusion=2))])
+def test_state_above_l2_size_against_the_oracle(dtype, cfg):
+    """24 qubits (128 MiB complex64, 256 MiB complex128: larger than the 126 MB
+    L2, so every pass streams the state from HBM) on a short circuit with 3
+    measurements: outcomes and amplitudes against the oracle."""
+    n = 24
+    c = W.ucc_circuit(n, seed=24, n_gadgets=None, w_lo=2, w_hi=6, theta="uniform", target_gates=400, n_meas=3)
+    ref = oracle.basis_state(n)
+    r = oracle.run(ref, n, c.gates, seed=9)
+    sim = qs.Sim(n, dtype, seed=9, config=cfg)
+    sim.apply(c.gates)
+    assert sim.sync() == 0
+    out, prob = sim.outcomes()
+    assert np.array_equal(out, r.outcomes)
+    got = sim.state()
+    if dtype == "c128":
+        assert np.abs(got - ref).max() <= 1e-10
+    else:
+        assert 1 - H.fidelity(ref, got) <= 1e-5
+    sim.close()
+
+
+def test_more_than_2_32_amplitudes_ghz_closed_form():
+    """33 qubits, complex64 (64 GiB): the GHZ circuit H(0), CX(0,1), ...,
+    CX(31,32) gives (|0...0> + |1...1>)/sqrt(2), so every qubit has P(0) = 1/2,
+    <Z_0 Z_32> = 1 and <X...X> (all 33 qubits) = 1; a measurement of qubit 32
+    then leaves the basis state of its outcome on every qubit.  Checks 64-bit
+    amplitude indexing in the tile, reduction, expectation and collapse
+    kernels without reading the state back."""
+    n = 33
+    if torch.cuda.mem_get_info()[0] < (72 << 30):
+        pytest.skip("needs 72 GiB of free device memory")
+    sim = qs.Sim(n, "c64", seed=4, config=dict(fusion=1))
+    sim.apply(W.ghz_circuit(n).gates)
+    assert sim.sync() == 0
+    for q in (0, 17, 32):
+        p0, p1 = sim.prob(q)
+        assert abs(p0 - 0.5) < 1e-6 and abs(p1 - 0.5) < 1e-6
+    terms = np.zeros(2, dtype=W.TERM_DTYPE)
+    terms[0] = (0, (1 << 0) | (1 << 32), 1.0)
+    terms[1] = ((1 << n) - 1, 0, 1.0)
+    e = sim.expect(terms)
+    assert abs(e[0] - 1) < 1e-5 and abs(e[1] - 1) < 1e-5
+    out, pr, st = sim.measure(32, 77)
+    assert st == 0 and abs(pr - 0.5) < 1e-6
+    assert out == (0 if oracle.draw(77, 0) < 0.5 else 1)   # the draw is far from 1/2
+    for q in (0, 16, 31):
+        p0, p1 = sim.prob(q)
+        assert (p0, p1) == ((1.0, 0.0) if out == 0 else (0.0, 1.0))
+    sim.close()

@@ -143,6 +143,34 @@ def test_measure_api_and_reset(dtype):
     assert abs(p0 - r0) < 1e-6 and abs(p1 - r1) < 1e-6
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,tile_bits,fusion", [(10, 0, 1), (16, 12, 1), (16, 12, 2)])
+def test_reset_with_outcome_one(dtype, n, tile_bits, fusion):
+    """RESET records whose outcome is 1, so the |1> half is moved onto |0>:
+    one drawn (the seed is picked on the oracle so that its first draw gives
+    1), one forced (qubit reset, flipped by X, reset again: p0 = 0).  Resident
+    (n = 10) and tiled (n = 16) paths, both fusion levels."""
+    q1, q2 = 2, n - 1
+    body = W.ucc_circuit(n, seed=60 + n, n_gadgets=20, w_lo=2, w_hi=5, target_gates=500).gates
+    tail = W.records([(OP["RESET"], q1, 0, 0, 0, 0), (OP["H"], 0, 0, 0, 0, 0), (OP["CX"], 0, q1, 0, 0, 0),
+                      (OP["RESET"], q2, 0, 0, 0, 0), (OP["X"], q2, 0, 0, 0, 0),
+                      (OP["RESET"], q2, 0, 0, 0, 0), (OP["RY"], q2, 0, 0.7, 0, 0)])
+    c = W.Circuit(n, np.concatenate([body, tail]))
+    seed = None
+    for s in range(200):
+        ref, r = run_oracle(c, seed=s)
+        if r.status == 0 and r.outcomes[0] == 1:
+            seed = s
+            break
+    assert seed is not None
+    assert list(r.outcomes[1:]) == [r.outcomes[1], 1]      # the forced reset gives 1
+    sim, st = run_gpu(c, dtype, seed=seed, config=dict(tile_bits=tile_bits, fusion=fusion))
+    assert st == 0
+    out, prob = sim.outcomes()
+    check_outcomes(dtype, out, prob, r, seed)
+    check_state(dtype, sim.state(), ref)
+
+
 @pytest.mark.parametrize("tile_bits", [0, 8])
 def test_assertion_mode_and_success_product(tile_bits):
     t = H.load_mma_table("tests/golden/mma_table.txt")
@@ -287,6 +315,36 @@ def test_rotation_passes_uniform_angles(n, tile_bits, persistent):
     out, prob = sim.outcomes()
     check_outcomes("c64", out, prob, r, 13)
     check_state("c64", sim.state(), ref)
+
+
+@pytest.mark.parametrize("dtype,n,fusion,tile_bits,forced_low,persistent", [
+    ("c64", 15, 2, 12, 3, 0), ("c64", 16, 2, 12, 2, 0), ("c64", 16, 2, 13, 3, 0),
+    ("c64", 16, 2, 12, 3, 1), ("c64", 15, 2, 13, 2, 1), ("c64", 15, 1, 12, 2, 0),
+    ("c128", 15, 2, 12, 2, 0), ("c128", 16, 1, 12, 2, 0), ("c128", 15, 2, 11, 1, 0)])
+def test_fewer_forced_low_qubits(dtype, n, fusion, tile_bits, forced_low, persistent):
+    """Tiles with fewer forced low qubits than the default (4 for complex64, 3
+    for complex128): shorter contiguous tile rows in the generic pass and the
+    register pass, and (persistent = 1) the fallback from resident-block
+    passes, which need 4, to one block per tile.  Amplitudes and outcomes
+    against the oracle."""
+    c = W.ucc_circuit(n, seed=90 + n + forced_low, n_gadgets=None, w_lo=2, w_hi=6, theta="uniform",
+                      target_gates=2500, n_meas=4)
+    ref, r = run_oracle(c, seed=17)
+    cfg = dict(fusion=fusion, tile_bits=tile_bits, forced_low=forced_low, persistent=persistent)
+    sim, st = run_gpu(c, dtype, seed=17, config=cfg)
+    assert st == 0
+    out, prob = sim.outcomes()
+    check_outcomes(dtype, out, prob, r, 17)
+    check_state(dtype, sim.state(), ref)
+    # the same program compiled once and replayed (graph launches on the second run)
+    sim2 = qs.Sim(n, dtype, config=cfg, seed=17)
+    prog = sim2.compile(c.gates)
+    for _ in range(2):
+        sim2.reset()
+        sim2.run(prog)
+        assert sim2.sync() == 0
+    check_state(dtype, sim2.state(), ref)
+    prog.free()
 
 
 def test_persistent_passes_replay_and_recover_after_a_failed_assertion():

@@ -1,5 +1,6 @@
 """OpenQASM 2.0 reader (qsim_parse_qasm, host only): records, broadcasting,
-user gates, the decompositions of ccx / cswap / sx against the oracle, errors."""
+user gates, the decompositions of ccx / cswap / sx / c3x / c4x / c3sqrtx /
+rccx / rc3x against the oracle and dense matrices, errors."""
 import math
 
 import numpy as np
@@ -97,6 +98,83 @@ def test_ccx_and_cswap_are_exact():
         for x in range(8):
             ref[perm(x)] = psi[x]
         assert np.abs(run_qasm(text, psi) - ref).max() < 1e-12
+
+
+def dense_of(text, n):
+    """The 2^n x 2^n matrix a program applies, column by column on the oracle."""
+    N = 1 << n
+    U = np.zeros((N, N), dtype=np.complex128)
+    for x in range(N):
+        e = np.zeros(N, dtype=np.complex128)
+        e[x] = 1
+        U[:, x] = run_qasm(text, e)
+    return U
+
+
+def controlled_dense(n, controls, target, u):
+    """|x> -> |x> unless every control bit is 1; then u acts on the target bit
+    (matrix written entry by entry from that definition)."""
+    N = 1 << n
+    M = np.zeros((N, N), dtype=np.complex128)
+    cm = sum(1 << c for c in controls)
+    for x in range(N):
+        if x & cm != cm:
+            M[x, x] = 1
+            continue
+        b = (x >> target) & 1
+        for r in range(2):
+            M[(x & ~(1 << target)) | (r << target), x] = u[r, b]
+    return M
+
+
+SQRT_X = np.array([[1 + 1j, 1 - 1j], [1 - 1j, 1 + 1j]]) / 2
+PAULI_X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+
+
+@pytest.mark.parametrize("gate,n,controls,target,u", [
+    ("c3x q[0], q[1], q[2], q[3];", 4, [0, 1, 2], 3, PAULI_X),
+    ("c3x q[3], q[0], q[2], q[1];", 4, [3, 0, 2], 1, PAULI_X),
+    ("c4x q[0], q[1], q[2], q[3], q[4];", 5, [0, 1, 2, 3], 4, PAULI_X),
+    ("c4x q[4], q[2], q[0], q[3], q[1];", 5, [4, 2, 0, 3], 1, PAULI_X),
+    ("c3sqrtx q[0], q[1], q[2], q[3];", 4, [0, 1, 2], 3, SQRT_X),
+    ("c3sqrtx q[2], q[3], q[1], q[0];", 4, [2, 3, 1], 0, SQRT_X),
+])
+def test_multi_controlled_gates_are_exact(gate, n, controls, target, u):
+    """The paper's gate table: C3X, C4X (X controlled by 3 / 4 qubits) and
+    C3XSQRTX (sqrt(X) = the matrix of `sx`, controlled by 3 qubits), exactly,
+    global phase included, against the matrix of their definition."""
+    U = dense_of(f"OPENQASM 2.0; qreg q[{n}]; " + gate, n)
+    assert np.abs(U - controlled_dense(n, controls, target, u)).max() < 1e-12
+    # c3sqrtx applied twice is c3x
+    if "sqrtx" in gate:
+        U2 = dense_of(f"OPENQASM 2.0; qreg q[{n}]; " + gate + gate, n)
+        assert np.abs(U2 - controlled_dense(n, controls, target, PAULI_X)).max() < 1e-12
+
+
+def test_relative_phase_toffolis():
+    """RCCX and RC3X (the paper's gate table: relative-phase CCX and 3-controlled
+    X) equal CCX / C3X followed by a diagonal of unit phases (the defining
+    property), with the phases of the OpenQASM 2.0 standard header: for rccx a, b, c
+    -i on |c b a> = |011>, +i on |111>, -1 on |101> after the Toffoli (index bit
+    q = qubit q); for rc3x a, b, c, d +i on |d c b a> = |0011>, -i on |1011>, -1 on
+    |1111> after the C3X."""
+    U = dense_of("OPENQASM 2.0; qreg q[3]; rccx q[0], q[1], q[2];", 3)
+    D = U @ controlled_dense(3, [0, 1], 2, PAULI_X).conj().T
+    assert np.abs(D - np.diag(np.diag(D))).max() < 1e-12
+    want = np.ones(8, dtype=np.complex128)
+    want[0b011], want[0b111], want[0b101] = -1j, 1j, -1
+    assert np.abs(np.diag(D) - want).max() < 1e-12
+    U = dense_of("OPENQASM 2.0; qreg q[4]; rc3x q[0], q[1], q[2], q[3];", 4)
+    D = U @ controlled_dense(4, [0, 1, 2], 3, PAULI_X).conj().T
+    assert np.abs(D - np.diag(np.diag(D))).max() < 1e-12
+    want = np.ones(16, dtype=np.complex128)
+    want[0b0011], want[0b1011], want[0b1111] = 1j, -1j, -1
+    assert np.abs(np.diag(D) - want).max() < 1e-12
+    # on other qubits and broadcast-free operands too
+    U = dense_of("OPENQASM 2.0; qreg q[4]; rccx q[3], q[1], q[0];", 4)
+    D = U @ controlled_dense(4, [3, 1], 0, PAULI_X).conj().T
+    assert np.abs(D - np.diag(np.diag(D))).max() < 1e-12
+    assert np.allclose(np.abs(np.diag(D)), 1)
 
 
 def test_sx_squares_to_x_and_sxdg_undoes_it():

@@ -34,15 +34,20 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving loop's slot streams need their own hardware queues; this only
+# takes effect if set before the process creates its CUDA context
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 # DRAM bytes (read + write) of one k_rot_pass launch of the 21-qubit circuit in
-# the configuration below, from one ncu capture of the current kernel (ncu
-# empties the caches before a replayed launch, so this is the state's cold
-# read; in the timed loop the state stays in L2); None: no capture yet.
+# the configuration below: dram__bytes_read.sum + dram__bytes_write.sum of the
+# current kernel from one ncu capture (3 launches of a 2M-gate prefix: 16.85 MB
+# read, 0 written, each); ncu empties the caches before a captured launch, so
+# this is the state's cold read; in the timed loop the state stays in L2.
 TRAFFIC_CONFIG = dict(fusion=2, k_max=2, tile_bits=12)
-TRAFFIC_PER_LAUNCH = None
-TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, k_rot_pass, 21 qubits, tile 12"
+TRAFFIC_PER_LAUNCH = 16854272
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, 21 qubits, tile 12 "
+                  "(caches emptied before the captured launch: the state's cold read; writes stay in L2)")
 # the large workload's metric and description, shared by both arms
 METRIC_LARGE = "gates/s at 21 qubits (UCC-style circuit)"
 WORKLOAD_LARGE = ("21-qubit UCC-style Trotter circuit (2,000 weight 2-6 Pauli exponentials per step, "
@@ -59,6 +64,9 @@ def parse():
                     help="gate count of the circuit (the named workload is 115,000,000)")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--k-max", type=int, default=2)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"],
+                    help="large workload: complex64 (FP32 gate arithmetic, the default) or complex128 "
+                         "(FP64 throughout, the paper's arithmetic)")
     ap.add_argument("--threads", type=int, default=0, choices=[0, 256, 512],
                     help="with --fusion >= 0: threads per block of the generic tile pass (256 / 512 also "
                          "keep dense passes out of register segments)")
@@ -386,7 +394,7 @@ def run_ours(args):
     sweep = None
     if args.fusion < 0:
         from paper_2310_17739_gb300 import autotune
-        cfg, entry = autotune.tune(n, c.gates, "c64", prefix=1_000_000, use_cache=False)
+        cfg, entry = autotune.tune(n, c.gates, args.dtype, prefix=1_000_000, use_cache=False)
         sweep = [dict(config=r["config"], gates_per_s=r["gates_per_s"], passes=r["passes"],
                       fused_ops=r["fused_ops"]) for r in entry["report"]]
     else:
@@ -397,7 +405,7 @@ def run_ours(args):
         if args.forced_low:
             cfg["forced_low"] = args.forced_low
     stream = torch.cuda.current_stream()
-    sim = qs.Sim(n, "c64", stream=stream, config=cfg, seed=1003)
+    sim = qs.Sim(n, args.dtype, stream=stream, config=cfg, seed=1003)
     t0 = time.perf_counter()
     prog = sim.compile(c.gates)
     t_compile = time.perf_counter() - t0
@@ -446,7 +454,7 @@ def run_ours(args):
     # end to end through the public API from host gate records
     e2e = None
     if not args.no_e2e:
-        sim2 = qs.Sim(n, "c64", stream=stream, config=cfg, seed=1003)
+        sim2 = qs.Sim(n, args.dtype, stream=stream, config=cfg, seed=1003)
         sim2.apply(c.gates[: min(c.G, 2_000_000)])
         sim2.sync()
         barrier()
@@ -469,7 +477,7 @@ def run_ours(args):
         sim.close()
         return
     hbm_peak, src = peaks()
-    l2_gbs = l2_copy_gbs(torch, n)
+    l2_gbs = l2_copy_gbs(torch, n + (1 if args.dtype == "c128" else 0))  # a buffer the size of the state
     n_s = max(prof["samples"], 1)
     avg_ms = prof["ms"] / n_s
     flops_l = prof["flops"] / n_s
@@ -478,7 +486,7 @@ def run_ours(args):
     gbs = bytes_l / (avg_ms / 1e3) / 1e9 if avg_ms else 0.0
     alu_frac = tflops / FP32_PEAK_TFLOPS
     mem_frac = gbs / hbm_peak
-    # The 16 MiB state stays in L2 for the whole step, so the bound of a pass
+    # The state (16 MiB complex64, 32 MiB complex128) stays in L2 for the whole step, so the bound of a pass
     # (one read and one write of the state) is L2 bandwidth, measured live.
     roof = {"bound": "l2", "achieved": gbs, "peak": l2_gbs, "unit": "GB/s", "frac": gbs / l2_gbs,
             "peak_source": "measured here: CUDA graph of 100 in-place copies of an L2-resident buffer the "
@@ -500,8 +508,9 @@ def run_ours(args):
         "metric": METRIC_LARGE,
         "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": "complex64 amplitudes, FP32 gate arithmetic, FP64 reductions/renormalisation",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.dtype == "c64" else "f64",
+        "precision": "complex64 amplitudes, FP32 gate arithmetic, FP64 reductions/renormalisation"
+                     if args.dtype == "c64" else "complex128 amplitudes, FP64 throughout",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_LARGE,
                    "n_qubits": 21, "gates": c.G, "measurements": info["measurements"],
@@ -512,8 +521,8 @@ def run_ours(args):
                    "autotune_sweep_1M_gate_prefix": sweep,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed before the timed region; each step streams the ~%.1f GB program "
-                         "(larger than L2); the 16 MiB state is L2-resident within a step by design"
-                         % (info["device_bytes"] / 1e9),
+                         "(larger than L2); the %d MiB state is L2-resident within a step by design"
+                         % (info["device_bytes"] / 1e9, (8 if args.dtype == "c64" else 16) << (n - 20)),
                    "compile_s": t_compile},
         "gpu_launches": launches,
         "roofline": roof,
@@ -525,7 +534,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.cpu_seconds)
     sim.close()
-    if world == 1 and not args.no_summaries:
+    if world == 1 and not args.no_summaries and args.dtype == "c64":
         # side measurements (outside the timed region): the same recipe above L2
         # size, the paper's complex128 arithmetic on a prefix, and the batched
         # and serving workloads (their own lines, nested)
@@ -747,7 +756,6 @@ def run_serving(args, nested=False):
     """Poisson arrivals (rate args.rate) for args.serve_seconds, served by the
     continuous-admission loop; requests are drawn from a seeded pool.
     nested: return the line instead of printing it."""
-    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")  # slot streams on separate queues
     world, rank, local = (1, 0, 0) if nested else dist_setup()
     import torch
     torch.cuda.set_device(local)

@@ -7,6 +7,7 @@
 #include <condition_variable>
 #include <deque>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -985,7 +986,7 @@ std::vector<size_t> chunk_bounds(const qsim_ctx *c, size_t ng) {
 
 // Register-segment layout for rotation passes: single-state launches with the
 // default thread count only (the multi-state kernel runs the generic pass).
-bool allow_reg(const qsim_ctx *c) { return c->cfg.threads == 0 && !c->multi_state; }
+bool allow_reg(const qsim_ctx *c) { return c->cfg.threads == 0; }
 
 int compile_threads(const qsim_ctx *c) {
     if (c->cfg.compile_threads > 0) return c->cfg.compile_threads;
@@ -1668,10 +1669,18 @@ struct qsim_batch {
     // wide (tiled) instances advance in lockstep: step k runs pass k of every
     // one of them in one multi-state launch (events as per-instance launches)
     struct Step {
-        size_t first = 0;       // into tiled_descs
+        size_t first = 0;       // generic passes: tiled_descs[first, first + count)
         int count = 0;
         uint32_t ctas = 0;
         int max_m = 1, kmax = 1;
+        struct RegGroup {       // register-segment passes of one tile size
+            size_t first = 0;
+            int count = 0;
+            uint32_t ctas = 0;
+            int m = 0;
+            bool dense = false;
+        };
+        std::vector<RegGroup> reg;
         std::vector<std::pair<int, Pass>> events;  // (instance, event pass)
     };
     bool plan_valid = false;
@@ -1921,66 +1930,76 @@ qsim_status build_tiled_plan(qsim_batch *b, bool may_upload) {
     qsim_ctx *c = b->aux;
     b->tiled_descs.clear();
     b->steps.clear();
+    // step k holds pass k of every wide instance
+    struct Item {
+        int i;
+        const DevChunk *dc;
+        const Pass *p;
+    };
+    std::vector<std::vector<Item>> per;
     for (int i = 0; i < b->count; i++) {
         if (b->resident[i]) continue;
-        qsim_ctx *ic = b->inst[i];
         size_t k = 0;
-        for (const DevChunk &dc : b->prog[i]) {
+        for (const DevChunk &dc : b->prog[i])
             for (const Pass &p : dc.passes) {
                 if (!p.ev && !p.count) continue;
-                if (b->steps.size() <= k) b->steps.resize(k + 1);
-                auto &st = b->steps[k];
-                if (p.ev) {
-                    st.events.emplace_back(i, p);
-                } else {
-                    qsim::TileArgs a;
-                    if (!qsim::make_tile_args(b->dtype, ic->state, ic->n, dc.m, p.tile, dc.bvec.data() + p.basis,
-                                              dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first,
-                                              p.mat_count, ic->ctl, &a) ||
-                        !qsim::generic_tile_ok(a))
-                        return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernel");
-                    a.wscale = p.gscale;
-                    a.pad = (uint32_t)std::max(dc.kmax, 1);  // op size, read back below
-                    b->tiled_descs.push_back(a);
-                    st.count++;
-                }
+                if (per.size() <= k) per.resize(k + 1);
+                per[k].push_back({i, &dc, &p});
                 k++;
             }
-        }
     }
-    // group the descriptors by step (they were appended instance-major)
-    std::vector<qsim::TileArgs> by_step;
-    by_step.reserve(b->tiled_descs.size());
-    {
-        std::vector<std::vector<qsim::TileArgs>> per(b->steps.size());
-        size_t pos = 0;
-        for (int i = 0; i < b->count; i++) {
-            if (b->resident[i]) continue;
-            size_t k = 0;
-            for (const DevChunk &dc : b->prog[i])
-                for (const Pass &p : dc.passes) {
-                    if (!p.ev && !p.count) continue;
-                    if (!p.ev) per[k].push_back(b->tiled_descs[pos++]);
-                    k++;
-                }
-        }
-        for (size_t k = 0; k < per.size(); k++) {
-            auto &st = b->steps[k];
-            st.first = by_step.size();
-            st.count = (int)per[k].size();
-            uint32_t ctas = 0;
-            for (auto &a : per[k]) {
-                a.cta_first = ctas;
-                ctas += 1u << (a.n - a.m);
-                st.max_m = std::max(st.max_m, a.m);
-                st.kmax = std::max(st.kmax, (int)a.pad);
-                a.pad = 0;
-                by_step.push_back(a);
+    b->steps.resize(per.size());
+    for (size_t k = 0; k < per.size(); k++) {
+        auto &st = b->steps[k];
+        // the generic passes of the step (one multi-state launch), then its
+        // register-segment passes grouped by (tile size, dense ops)
+        st.first = b->tiled_descs.size();
+        uint32_t ctas = 0;
+        std::map<std::pair<int, int>, std::vector<qsim::TileArgs>> regs;
+        for (const Item &it : per[k]) {
+            if (it.p->ev) {
+                st.events.emplace_back(it.i, *it.p);
+                continue;
             }
-            st.ctas = ctas;
+            qsim_ctx *ic = b->inst[it.i];
+            const DevChunk &dc = *it.dc;
+            const Pass &p = *it.p;
+            qsim::TileArgs a;
+            if (!qsim::make_tile_args(b->dtype, ic->state, ic->n, dc.m, p.tile, dc.bvec.data() + p.basis,
+                                      dc.d_ops + p.first, p.count, dc.d_mats, (uint32_t)p.mat_first, p.mat_count,
+                                      ic->ctl, &a))
+                return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernels");
+            if (p.reg) {
+                a.scale = p.scale;
+                regs[std::make_pair(dc.m, p.reg == 2 ? 1 : 0)].push_back(a);
+                continue;
+            }
+            if (!qsim::generic_tile_ok(a)) return bfail(b, QSIM_E_INVAL, "pass does not fit the tile kernel");
+            a.wscale = p.gscale;
+            a.cta_first = ctas;
+            ctas += 1u << (a.n - a.m);
+            st.max_m = std::max(st.max_m, a.m);
+            st.kmax = std::max(st.kmax, std::max(dc.kmax, 1));
+            b->tiled_descs.push_back(a);
+            st.count++;
+        }
+        st.ctas = ctas;
+        for (auto &g : regs) {
+            qsim_batch::Step::RegGroup rg;
+            rg.first = b->tiled_descs.size();
+            rg.count = (int)g.second.size();
+            rg.m = g.first.first;
+            rg.dense = g.first.second != 0;
+            uint32_t rc = 0;
+            for (auto &a : g.second) {
+                a.cta_first = rc;
+                rc += 1u << (a.n - a.m);
+                b->tiled_descs.push_back(a);
+            }
+            rg.ctas = rc;
+            st.reg.push_back(rg);
         }
     }
-    b->tiled_descs.swap(by_step);
     if (!b->tiled_descs.empty()) {
         if (!may_upload) return bfail(b, QSIM_E_STATE, "batch plan changed during capture");
         const size_t need = b->tiled_descs.size();
@@ -2079,6 +2098,9 @@ qsim_status enqueue_run(qsim_batch *b, bool upload_table) {
             CK(qsim::launch_tile_pass_multi(b->dtype, threads, st.kmax, b->d_descs + st.first, st.count,
                                             st.ctas, st.max_m, b->stream),
                "multi-state tile pass launch");
+        for (const auto &rg : st.reg)
+            CK(qsim::launch_rot_pass_multi(b->d_descs + rg.first, rg.count, rg.ctas, rg.m, rg.dense, b->stream),
+               "multi-state register pass launch");
         for (const auto &ev : st.events) {
             qsim_ctx *ic = b->inst[ev.first];
             qsim_status s = launch_measure(ic, (int)ev.second.q, ev.second.flags,

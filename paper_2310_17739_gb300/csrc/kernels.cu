@@ -53,6 +53,34 @@ __device__ __forceinline__ double norm2(float2 a) {
     return x * x + y * y;
 }
 __device__ __forceinline__ double norm2(double2 a) { return a.x * a.x + a.y * a.y; }
+// |a|^2 as a term of an FP64 sum.  complex64: formed in FP32 (the amplitude's
+// own precision, relative error <= 2^-23), then widened, so each term costs
+// one FP64-pipe operation of the sum (GB300's FP64 rate is 1/60 of FP32's);
+// complex128: in FP64.
+__device__ __forceinline__ double norm2_term(float2 a) { return (double)fmaf(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double norm2_term(double2 a) { return norm2(a); }
+// Re(i^ny conj(b) a) (-1)^neg as a term of an FP64 sum, formed in the
+// amplitudes' precision as norm2_term is.
+__device__ __forceinline__ double pauli_term(float2 a, float2 b, int ny, unsigned neg) {
+    const float wr = fmaf(b.x, a.x, b.y * a.y), wi = fmaf(b.x, a.y, -(b.y * a.x));
+    float v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
+    v = __int_as_float(__float_as_int(v) ^ (neg << 31));
+    return (double)v;
+}
+__device__ __forceinline__ double pauli_term(double2 a, double2 b, int ny, unsigned neg) {
+    const double wr = b.x * a.x + b.y * a.y, wi = b.x * a.y - b.y * a.x;
+    const double v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
+    return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)neg << 63));
+}
+// w with its sign flipped when neg = 1, by integer operations on the sign bit
+// (no floating-point instruction: on the FP64 pipe that would cost as much as
+// the rotation's fused multiply-adds).
+__device__ __forceinline__ float flip_sign(float w, unsigned neg) {
+    return __int_as_float(__float_as_int(w) ^ (neg << 31));
+}
+__device__ __forceinline__ double flip_sign(double w, unsigned neg) {
+    return __longlong_as_double(__double_as_longlong(w) ^ ((unsigned long long)neg << 63));
+}
 __device__ __forceinline__ float2 scale_by(float2 a, double s) {
     return make_float2((float)((double)a.x * s), (float)((double)a.y * s));
 }
@@ -321,43 +349,40 @@ __device__ __forceinline__ void apply_dense_smem(T *tile, int m, const DevOp &op
 // tile-local X and Z masks, b = parity(zc & tile index), u = +-W,
 //   a'_j = cos a_j + W (odd ? i : 1) (-1)^{parity(k & z) ^ b} a_k,   k = j ^ x.
 // With x = 0 it is diagonal: a'_j = (cos + W (odd ? i : 1) (-1)^{parity(j & z) ^ b}) a_j.
-template <typename T, int NT>
-__device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, const T *mats, uint32_t bid) {
-    const unsigned x = op.lq[0] | ((unsigned)op.lq[1] << 8);
-    const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
-    const bool odd = op.lq[4] & 1;
-    const uint32_t zc = op.flags | ((uint32_t)op.pad << 16);
-    const bool scaled = op.lq[4] & 2;
-    const T cs = mats[op.mat];
-    const auto c = cs.x;
-    const auto w = (__popc(zc & bid) & 1) ? -cs.y : cs.y;
-    const unsigned Nt = 1u << m;
-    // (c, w) pair update: r = c a + u (odd ? i : 1) b; scaled form (c = 1):
-    // r = a + u (odd ? i : 1) b, one fused multiply-add per component
-    auto upd = [odd, scaled, c](T a, T b, decltype(c) u) {
-        T r;
-        if (scaled) {
-            if (odd) {
-                r.x = fma_r(-u, b.y, a.x);
-                r.y = fma_r(u, b.x, a.y);
-            } else {
-                r.x = fma_r(u, b.x, a.x);
-                r.y = fma_r(u, b.y, a.y);
-            }
-        } else if (odd) {
-            r.x = c * a.x - u * b.y;
-            r.y = c * a.y + u * b.x;
+// (c, w) pair update r = c a + u (odd ? i : 1) b, or in the scaled form (c = 1)
+// r = a + u (odd ? i : 1) b, one fused multiply-add per component.  SCALED and
+// ODD are compile-time, so each pair loop holds only its own arithmetic (with
+// run-time flags the arms were all evaluated and selected, tripling the FP64
+// work of complex128 rotations).
+template <bool SCALED, bool ODD, typename T, typename R>
+__device__ __forceinline__ T pauli_upd(T a, T b, R c, R u) {
+    T r;
+    if (SCALED) {
+        if (ODD) {
+            r.x = fma_r(-u, b.y, a.x);
+            r.y = fma_r(u, b.x, a.y);
         } else {
-            r.x = c * a.x + u * b.x;
-            r.y = c * a.y + u * b.y;
+            r.x = fma_r(u, b.x, a.x);
+            r.y = fma_r(u, b.y, a.y);
         }
-        return r;
-    };
+    } else if (ODD) {
+        r.x = c * a.x - u * b.y;
+        r.y = c * a.y + u * b.x;
+    } else {
+        r.x = c * a.x + u * b.x;
+        r.y = c * a.y + u * b.y;
+    }
+    return r;
+}
+
+template <bool SCALED, bool ODD, typename T, int NT, typename R>
+__device__ __forceinline__ void pauli_pass(T *tile, int m, unsigned x, unsigned z, R c, R w) {
+    const unsigned Nt = 1u << m;
     if (x == 0) {
         for (unsigned j = threadIdx.x; j < Nt; j += NT) {
-            const auto u = (__popc(j & z) & 1) ? -w : w;
+            const R u = flip_sign(w, __popc(j & z) & 1u);
             const T a = tile[j];
-            tile[j] = upd(a, a, u);
+            tile[j] = pauli_upd<SCALED, ODD>(a, a, c, u);
         }
         return;
     }
@@ -380,11 +405,30 @@ __device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, con
         for (int u = 0; u < U; u++) {
             if (g0 + u * NT >= P) break;
             const unsigned j = jj[u], k = j ^ x;
-            const auto wk = (__popc(k & z) & 1) ? -w : w;  // W (-1)^{parity(k & z) ^ b}
-            const auto wj = (__popc(j & z) & 1) ? -w : w;
-            tile[j] = upd(aj[u], ak[u], wk);
-            tile[k] = upd(ak[u], aj[u], wj);
+            const R wk = flip_sign(w, __popc(k & z) & 1u);  // W (-1)^{parity(k & z) ^ b}
+            const R wj = flip_sign(w, __popc(j & z) & 1u);
+            tile[j] = pauli_upd<SCALED, ODD>(aj[u], ak[u], c, wk);
+            tile[k] = pauli_upd<SCALED, ODD>(ak[u], aj[u], c, wj);
         }
+    }
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void apply_pauli(T *tile, int m, const DevOp &op, const T *mats, uint32_t bid) {
+    const unsigned x = op.lq[0] | ((unsigned)op.lq[1] << 8);
+    const unsigned z = op.lq[2] | ((unsigned)op.lq[3] << 8);
+    const bool odd = op.lq[4] & 1;
+    const uint32_t zc = op.flags | ((uint32_t)op.pad << 16);
+    const bool scaled = op.lq[4] & 2;
+    const T cs = mats[op.mat];
+    const auto c = cs.x;
+    const auto w = flip_sign(cs.y, __popc(zc & bid) & 1u);
+    if (scaled) {
+        if (odd) pauli_pass<true, true, T, NT>(tile, m, x, z, c, w);
+        else pauli_pass<true, false, T, NT>(tile, m, x, z, c, w);
+    } else {
+        if (odd) pauli_pass<false, true, T, NT>(tile, m, x, z, c, w);
+        else pauli_pass<false, false, T, NT>(tile, m, x, z, c, w);
     }
 }
 
@@ -803,23 +847,23 @@ __device__ __forceinline__ void seg_load_smem(float2 *reg, uint32_t addr, const 
     }
 }
 
-template <int NT, int MINB, bool DENSE>
-__global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// One register-segment pass over tile `bid` of the pass described by `a`, run by
+// blockDim.x = 2^(m-5) threads.
+template <bool DENSE>
+__device__ __forceinline__ void rot_pass_body(const TileArgs &a, const uint32_t bid, unsigned char *smem_raw,
+                                              uint32_t *bv_s) {
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     float2 *mats_s = tile + (1u << a.m);
     DevOp *ops_s = reinterpret_cast<DevOp *>(mats_s + kPassMats);
-    __shared__ uint32_t bv_s[16];
     grid_dep_launch_next();
-    const unsigned tid = threadIdx.x, nt = blockDim.x;  // 2^(m-5) threads (NT is the most)
+    const unsigned tid = threadIdx.x, nt = blockDim.x;  // 2^(m-5) threads
     for (unsigned i = tid; i < a.n_ops; i += nt) cp_async16(ops_s + i, a.ops + i);
     {
         const float2 *gm = reinterpret_cast<const float2 *>(a.mats) + a.mat_first;
         for (unsigned i = tid; i < a.mat_count; i += nt) cp_async8(mats_s + i, gm + i);
     }
     if (tid < 16) bv_s[tid] = (uint32_t)a.bv[tid];  // n <= 32: amplitude indices fit 32 bits
-    const uint32_t bid = blockIdx.x;
-    uint32_t x0 = 0;  // the tile's origin: blockIdx spread over the non-pivot positions
+    uint32_t x0 = 0;  // the tile's origin: the tile number spread over the non-pivot positions
     for (int j = 0; j < a.n - a.m; j++) x0 |= ((bid >> j) & 1u) << a.ntq[j];
     cp_async_wait_all();
     grid_dep_wait();
@@ -884,6 +928,35 @@ __global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
         for (int j = 0; j < 5; j++) sd_prev[j] = sd[j];
         i += 1 + nseg;
     }
+}
+
+template <int NT, int MINB, bool DENSE>
+__global__ void __launch_bounds__(NT, MINB) k_rot_pass(TileArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t bv_s[16];
+    rot_pass_body<DENSE>(a, blockIdx.x, smem_raw, bv_s);
+}
+
+// Register-segment passes of several independent states in one launch (all
+// with the same tile size m: blockDim.x = 2^(m-5)): descs[j] covers blocks
+// [cta_first_j, cta_first_{j+1}); each block finds its state's pass by binary
+// search and runs it on tile (blockIdx.x - cta_first_j).
+template <int NT, int MINB, bool DENSE>
+__global__ void __launch_bounds__(NT, MINB) k_rot_pass_multi(const TileArgs *descs, int n_desc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t bv_s[16];
+    __shared__ TileArgs d;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_desc - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].cta_first <= blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        d = descs[lo];
+    }
+    __syncthreads();
+    rot_pass_body<DENSE>(d, blockIdx.x - d.cta_first, smem_raw, bv_s);
 }
 
 // --------------------------------------------------- final-state shots --
@@ -1199,7 +1272,7 @@ __device__ void run_resident(const Instance &in, T *tile, double *red, int *bcas
         const int q = op.lq[0];
         double s0 = 0, s1 = 0;
         for (unsigned l = threadIdx.x; l < N; l += NT) {
-            const double w = norm2(tile[l]);
+            const double w = norm2_term(tile[l]);
             if ((l >> q) & 1u) s1 += w;
             else s0 += w;
         }
@@ -1289,7 +1362,7 @@ __global__ void __launch_bounds__(kRedThreads) k_prob(const void *state, int n, 
     double s0 = 0, s1 = 0;
     for (uint64_t l = threadIdx.x; l < chunk; l += kRedThreads) {
         const uint64_t i = start + l;
-        const double w = norm2(st[i]);
+        const double w = norm2_term(st[i]);
         if ((i >> a.q) & 1ull) s1 += w;
         else s0 += w;
     }
@@ -1367,14 +1440,8 @@ __global__ void __launch_bounds__(256) k_expect(const void *state, int n, const 
     double acc = 0, dummy = 0;
     for (uint64_t l = threadIdx.x; l < chunk; l += 256) {
         const uint64_t j = start + l;
-        const double2 aj = to_d(st[j]), ax = to_d(st[j ^ x]);
-        // w = conj(a_{j^x}) * a_j
-        const double wr = ax.x * aj.x + ax.y * aj.y;
-        const double wi = ax.x * aj.y - ax.y * aj.x;
-        // Re(i^ny * w)
-        double v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
-        if (__popcll(j & z) & 1) v = -v;
-        acc += v;
+        // Re(i^ny conj(a_{j^x}) a_j) (-1)^{parity(j & z)}
+        acc += pauli_term(st[j], st[j ^ x], ny, __popcll(j & z) & 1u);
     }
     block_sum2<256>(acc, dummy, red);
     if (threadIdx.x == 0) partials[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
@@ -1394,12 +1461,7 @@ __global__ void __launch_bounds__(256) k_expect_batch(const ExpectJob *jobs) {
         const int ny = __popcll(x & z) & 3;
         double acc = 0, dummy = 0;
         for (uint64_t j = threadIdx.x; j < N; j += 256) {
-            const double2 aj = to_d(st[j]), ax = to_d(st[j ^ x]);
-            const double wr = ax.x * aj.x + ax.y * aj.y;
-            const double wi = ax.x * aj.y - ax.y * aj.x;
-            double v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
-            if (__popcll(j & z) & 1) v = -v;
-            acc += v;
+            acc += pauli_term(st[j], st[j ^ x], ny, __popcll(j & z) & 1u);
         }
         block_sum2<256>(acc, dummy, red);
         if (threadIdx.x == 0) jb.out[t] = __longlong_as_double((long long)jb.terms[3 * t + 2]) * acc;
@@ -1457,6 +1519,12 @@ cudaError_t setup_kernels() {
     QSIM_ATTR((k_rot_pass<128, 4, true>));
     QSIM_ATTR((k_rot_pass<256, 2, true>));
     QSIM_ATTR((k_rot_pass<512, 1, true>));
+    QSIM_ATTR((k_rot_pass_multi<128, 4, false>));
+    QSIM_ATTR((k_rot_pass_multi<256, 2, false>));
+    QSIM_ATTR((k_rot_pass_multi<512, 1, false>));
+    QSIM_ATTR((k_rot_pass_multi<128, 4, true>));
+    QSIM_ATTR((k_rot_pass_multi<256, 2, true>));
+    QSIM_ATTR((k_rot_pass_multi<512, 1, true>));
     QSIM_ATTR(k_rot_pipe<64>);
     QSIM_ATTR(k_rot_pipe<128>);
     QSIM_ATTR(k_rot_pipe<256>);
@@ -1581,6 +1649,24 @@ cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const ui
     if (m == 12) return launch_dependent(k_rot_pass<128, 4, false>, grid, threads, smem, s, a);
     if (m <= 13) return launch_dependent(k_rot_pass<256, 2, false>, grid, threads, smem, s, a);
     return launch_dependent(k_rot_pass<512, 1, false>, grid, threads, smem, s, a);
+}
+
+cudaError_t launch_rot_pass_multi(const TileArgs *d_descs, int n_desc, uint32_t total_ctas, int m, bool dense,
+                                  cudaStream_t s) {
+    if (n_desc <= 0 || total_ctas == 0) return cudaSuccess;
+    if (m < 10 || m > 14) return cudaErrorInvalidValue;
+    const unsigned threads = 1u << (m - 5);
+    const size_t smem = tile_smem_bytes(0, m);
+    if (dense) {
+        if (m == 12) k_rot_pass_multi<128, 4, true><<<total_ctas, threads, smem, s>>>(d_descs, n_desc);
+        else if (m <= 13) k_rot_pass_multi<256, 2, true><<<total_ctas, threads, smem, s>>>(d_descs, n_desc);
+        else k_rot_pass_multi<512, 1, true><<<total_ctas, threads, smem, s>>>(d_descs, n_desc);
+    } else {
+        if (m == 12) k_rot_pass_multi<128, 4, false><<<total_ctas, threads, smem, s>>>(d_descs, n_desc);
+        else if (m <= 13) k_rot_pass_multi<256, 2, false><<<total_ctas, threads, smem, s>>>(d_descs, n_desc);
+        else k_rot_pass_multi<512, 1, false><<<total_ctas, threads, smem, s>>>(d_descs, n_desc);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rot_pipe(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,

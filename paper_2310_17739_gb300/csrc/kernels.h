@@ -134,6 +134,12 @@ bool generic_tile_ok(const TileArgs &a);
 cudaError_t launch_rot_pass(void *state, int n, int m, uint64_t pivots, const uint64_t *basis,
                             const DevOp *ops, uint32_t n_ops, const void *mats, uint32_t mat_first,
                             uint32_t mat_count, float scale, bool dense, const MeasCtl *ctl, cudaStream_t s);
+// Register-segment passes of several states in one launch: descs[0..n_desc)
+// in device memory with increasing cta_first, each made by make_tile_args
+// (with its scale) for a register-segment pass of tile size m (all equal);
+// dense as for launch_rot_pass (any of them holds RegDense ops).
+cudaError_t launch_rot_pass_multi(const TileArgs *d_descs, int n_desc, uint32_t total_ctas, int m, bool dense,
+                                  cudaStream_t s);
 // The same pass with resident blocks taking tiles from the device counter
 // *ctr (numbers base .. base + 2^(n-m) - 1 are this pass's tiles), each
 // prefetching its next tile while it computes the current one.  A launch

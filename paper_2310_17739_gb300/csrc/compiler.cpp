@@ -420,11 +420,13 @@ int tile_bits_for(const Config &cfg, int n, qsim_dtype dtype) {
         // rotation passes (register segments) run fastest on 12-dimensional
         // tiles from 16 qubits up (measured on one GB300 for 12-22 qubits:
         // 16q 18.2 vs 13.8 M gates/s at m = 10, 21q 12.0 vs 11.4 at m = 13,
-        // 22q 7.1 vs 5.5 at m = 14) and on 10-11-dimensional ones below; other
-        // passes take the largest tile that still leaves >= 256 tiles to spread
-        // over 152 SMs.
+        // 22q 7.1 vs 5.5 at m = 14) and on 10-11-dimensional ones below;
+        // complex128 rotation passes at most 12 (two blocks per SM: 1.30 vs 1.21
+        // M gates/s at 21q, m = 12 vs 13); other passes take the largest tile
+        // that still leaves >= 256 tiles to spread over 152 SMs.
         if (n <= 10) return n;
         if (dtype == QSIM_C64 && cfg.fusion == 2) m = std::max(10, std::min(12, n - 4));
+        else if (cfg.fusion == 2) m = std::max(10, std::min(12, n - 8));
         else m = std::max(10, std::min(mx, n - 8));
     }
     m = std::min(m, mx);

@@ -495,8 +495,9 @@ def test_inverse_records_undo_the_circuit():
 @pytest.mark.parametrize("n", [11, 12, 14, 15, 16, 18, 21, 22])
 def test_default_tile_size_rule(n):
     """tile_bits = 0: complex64 Pauli-rotation programs (fusion 2) take
-    min(12, max(10, n - 4))-dimensional tiles; other programs the largest tile
-    that leaves >= 256 tiles (n - 8, at least 10, at most the dtype's limit)."""
+    min(12, max(10, n - 4))-dimensional tiles, complex128 ones min(12, max(10,
+    n - 8)); other programs the largest tile that leaves >= 256 tiles (n - 8, at
+    least 10, at most the dtype's limit)."""
     from paper_2310_17739_gb300 import qsim as qs
     c = W.ucc_circuit(n, seed=7, n_gadgets=None, w_lo=2, w_hi=4, theta="uniform", target_gates=300, n_meas=0)
     tiles = [bin(p[0]).count("1") for p in qs.schedule(n, c.gates, dtype=qs.C64, fusion=2) if p[0]]
@@ -504,6 +505,8 @@ def test_default_tile_size_rule(n):
     tiles = [bin(p[0]).count("1") for p in qs.schedule(n, c.gates, dtype=qs.C64, fusion=1) if p[0]]
     assert tiles and set(tiles) == {min(14, max(10, n - 8))}
     tiles = [bin(p[0]).count("1") for p in qs.schedule(n, c.gates, dtype=qs.C128, fusion=2) if p[0]]
+    assert tiles and set(tiles) == {min(12, max(10, n - 8))}
+    tiles = [bin(p[0]).count("1") for p in qs.schedule(n, c.gates, dtype=qs.C128, fusion=1) if p[0]]
     assert tiles and set(tiles) == {min(13, max(10, n - 8))}
 
 

@@ -409,6 +409,30 @@ def test_long_run_of_one_rotation_falls_back_to_the_generic_pass():
     check_state("c64", sim.state(), ref)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_scaled_rotations_stop_before_the_product_of_cosines_underflows(dtype):
+    """300 repeats of one Pauli rotation at angles near pi/4 (cos ~ 0.71, so the
+    product of 300 cosines is ~1e-45) in one pass: the scaled form a + (W/cos)(...)
+    is used only while the product stays >= 2^-40 (the unscaled amplitudes stay
+    below 2^40), the rest of the pass runs unscaled; the state must match the
+    oracle.  Register and generic tile kernels (complex64), generic (complex128)."""
+    n = 16
+    rows = []
+    for r in range(300):
+        rows += W.gadget_rows([1, 6, 11], "XZY", (0.785 if r % 2 else -0.7) + 0.001 * (r % 7))
+    g = W.records([(op, q0, q1, p, 0, 0) for op, q0, q1, p in rows])
+    c = W.Circuit(n, np.concatenate([W.ucc_circuit(n, seed=9, n_gadgets=20, w_lo=2, w_hi=5,
+                                                   target_gates=400).gates, g]))
+    ref, _ = run_oracle(c)
+    for tb in (12, 10):
+        sim, st = run_gpu(c, dtype, config=dict(fusion=2, tile_bits=tb))
+        assert st == 0
+        got = sim.state()
+        assert np.all(np.isfinite(got))
+        check_state(dtype, got, ref)
+        sim.close()
+
+
 def test_profile_windows_count_launches_and_bytes():
     """Launch timing windows: every tile-pass launch inside a window is counted
     once with one read and one write of the state; windows close at

@@ -293,6 +293,16 @@ QSIM_API qsim_status qsim_sample(qsim_ctx *ctx, uint64_t qubit_mask, uint64_t sh
 QSIM_API qsim_status qsim_state(qsim_ctx *ctx, void *dst, size_t bytes, int dst_is_device);
 QSIM_API qsim_status qsim_set_state(qsim_ctx *ctx, const void *src, size_t bytes, int src_is_device);
 QSIM_API qsim_status qsim_reset_state(qsim_ctx *ctx);
+/* Checkpoint / resume.  The draw of the k-th measurement depends only on
+ * (seed, k) (see qsim_measure), so a run resumes exactly from a saved state
+ * (qsim_state), the seed and the ordinal of the next draw: a context given
+ * that state (qsim_set_state), seed (qsim_set_seed) and ordinal draws what the
+ * original context would have drawn next.  get: the ordinal the next MEASURE /
+ * RESET record or qsim_measure call will use (the number of draws since the
+ * last qsim_reset_state, unless set); set: make the next draw use ordinal k.
+ * Neither synchronises; set applies to work enqueued after it. */
+QSIM_API qsim_status qsim_get_draw_ordinal(const qsim_ctx *ctx, uint64_t *k);
+QSIM_API qsim_status qsim_set_draw_ordinal(qsim_ctx *ctx, uint64_t k);
 /* Device pointer of the state (valid until qsim_destroy) and its size. */
 QSIM_API qsim_status qsim_state_ptr(qsim_ctx *ctx, void **dptr, size_t *bytes);
 /* ---------------------------------------------------------------- timing --

@@ -1497,6 +1497,18 @@ qsim_status qsim_reset_state(qsim_ctx *c) {
     return QSIM_OK;
 }
 
+qsim_status qsim_get_draw_ordinal(const qsim_ctx *c, uint64_t *k) {
+    if (!c || !k) return QSIM_E_INVAL;
+    *k = c->ordinal;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_draw_ordinal(qsim_ctx *c, uint64_t k) {
+    if (!c) return fail(nullptr, QSIM_E_INVAL, "null context");
+    c->ordinal = k;
+    return QSIM_OK;
+}
+
 qsim_status qsim_state_ptr(qsim_ctx *c, void **dptr, size_t *bytes) {
     if (!c || !dptr) return fail(c, QSIM_E_INVAL, "null argument");
     *dptr = c->state;

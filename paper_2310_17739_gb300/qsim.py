@@ -79,6 +79,8 @@ _SIGS = {
     "qsim_state_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)], _i32),
     "qsim_sync": ([_vp], _i32),
     "qsim_sync_timeout": ([_vp, _dbl], _i32),
+    "qsim_get_draw_ordinal": ([_vp, ctypes.POINTER(_u64)], _i32),
+    "qsim_set_draw_ordinal": ([_vp, _u64], _i32),
     "qsim_config_init": ([ctypes.POINTER(QsimConfig)], None),
     "qsim_server_cancel": ([_vp, _u64], _i32),
     "qsim_batch_create": ([_i32, _vp, _i32, _vp, ALLOC_FN, FREE_FN, _vp, ctypes.POINTER(_vp)], _i32),
@@ -330,6 +332,15 @@ class Sim:
 
     def sync(self):
         return _lib.qsim_sync(self.h)
+
+    def draw_ordinal(self) -> int:
+        """Ordinal of the next measurement draw (checkpoint / resume)."""
+        k = ctypes.c_uint64()
+        _check(_lib.qsim_get_draw_ordinal(self.h, ctypes.byref(k)), self.h)
+        return k.value
+
+    def set_draw_ordinal(self, k: int):
+        _check(_lib.qsim_set_draw_ordinal(self.h, int(k)), self.h)
 
     def sync_timeout(self, seconds: float):
         """qsim_sync with a bounded wait: E_TIMEOUT if the work is still running."""

@@ -39,15 +39,23 @@ sys.path.insert(0, ROOT)
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
-# DRAM bytes (read + write) of one k_rot_pass launch of the 21-qubit circuit in
-# the configuration below: dram__bytes_read.sum + dram__bytes_write.sum of the
-# current kernel from one ncu capture (3 launches of a 2M-gate prefix: 16.85 MB
-# read, 0 written, each); ncu empties the caches before a captured launch, so
-# this is the state's cold read; in the timed loop the state stays in L2.
+# DRAM bytes (read + write) of one k_rot_pass launch in the configuration below,
+# per (qubits, dtype): dram__bytes_read.sum + dram__bytes_write.sum of the
+# current kernel from one ncu capture of 3 launches, averaged.  ncu empties the
+# caches before a captured launch.
+# * 21 qubits: a 2M-gate prefix; 16.85 MB read, 0 written, per launch.  This is
+#   the state's cold read; in the timed loop the 16 MiB state stays in L2.
+# * 26 qubits: 536.97 MB read and 473.8 MB written per launch.  The state is
+#   512 MiB, so a pass streams it from HBM once and back once; the ~63 MB of
+#   writes not counted are dirty lines still in L2 when the launch ends.
 TRAFFIC_CONFIG = dict(fusion=2, k_max=2, tile_bits=12)
-TRAFFIC_PER_LAUNCH = 16854272
-TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, 21 qubits, tile 12 "
-                  "(caches emptied before the captured launch: the state's cold read; writes stay in L2)")
+TRAFFIC = {
+    (21, "c64"): (16854272, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, 21 qubits, tile 12 "
+                            "(caches emptied before the captured launch: the state's cold read; writes stay in L2)"),
+    (26, "c64"): (1010739285, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_rot_pass, 26 qubits, tile 12, "
+                              "mean of 3 launches (one read and ~0.88 of one write of the 512 MiB state; the rest "
+                              "of the writes are dirty lines still in L2 at the launch's end)"),
+}
 # the large workload's metric and description, shared by both arms
 METRIC_LARGE = "gates/s at 21 qubits (UCC-style circuit)"
 WORKLOAD_LARGE = ("21-qubit UCC-style Trotter circuit (2,000 weight 2-6 Pauli exponentials per step, "
@@ -496,7 +504,10 @@ def run_ours(args):
         sim.close()
         return
     hbm_peak, src = peaks()
-    l2_gbs = l2_copy_gbs(torch, n + (1 if args.dtype == "c128" else 0))  # a buffer the size of the state
+    state_bytes = (8 if args.dtype == "c64" else 16) << n
+    fits_l2 = state_bytes <= (64 << 20)
+    # a buffer the size of the state; meaningless (an HBM copy) for a state larger than L2
+    l2_gbs = l2_copy_gbs(torch, n + (1 if args.dtype == "c128" else 0)) if fits_l2 else None
     n_s = max(prof["samples"], 1)
     avg_ms = prof["ms"] / n_s
     flops_l = prof["flops"] / n_s
@@ -508,9 +519,8 @@ def run_ours(args):
     # The 21-qubit state (16 MiB complex64, 32 MiB complex128) stays in L2 for the
     # whole step, so the bound of a pass (one read and one write of the state) is
     # L2 bandwidth, measured live; a state larger than L2 is bound by HBM.
-    state_bytes = (8 if args.dtype == "c64" else 16) << n
-    traffic_ok = cfg == TRAFFIC_CONFIG and n == 21 and args.dtype == "c64"
-    if state_bytes <= (64 << 20):
+    traffic = TRAFFIC.get((n, args.dtype)) if cfg == TRAFFIC_CONFIG else None
+    if fits_l2:
         roof = {"bound": "l2", "achieved": gbs, "peak": l2_gbs, "unit": "GB/s", "frac": gbs / l2_gbs,
                 "peak_source": "measured here: CUDA graph of 100 in-place copies of an L2-resident buffer the "
                                "size of the state (read + write bytes), best of 5"}
@@ -518,8 +528,8 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs); the state is larger than L2"}
     roof.update({
-            "traffic": TRAFFIC_PER_LAUNCH if traffic_ok else None,
-            "traffic_source": TRAFFIC_SOURCE if traffic_ok else "no capture of this configuration",
+            "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else "no capture of this configuration",
             "kernel": "tile passes: k_rot_pass (register segments) and k_tile_pass",
             "avg_launch_ms": avg_ms, "launch_samples": prof["samples"],
             "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
@@ -547,9 +557,11 @@ def run_ours(args):
                    "compile_config": cfg,
                    "autotune_sweep_1M_gate_prefix": sweep,
                    "parallelism": f"replicas x{world}",
-                   "l2": "flushed before the timed region; each step streams the ~%.1f GB program "
-                         "(larger than L2); the %d MiB state is L2-resident within a step by design"
-                         % (info["device_bytes"] / 1e9, (8 if args.dtype == "c64" else 16) << (n - 20)),
+                   "l2": ("flushed before the timed region; each step streams the ~%.1f GB program "
+                          "(larger than L2); the %d MiB state is L2-resident within a step by design"
+                          % (info["device_bytes"] / 1e9, state_bytes >> 20)) if fits_l2 else
+                         ("flushed before the timed region; the %d MiB state is larger than L2, so every "
+                          "pass streams it from HBM" % (state_bytes >> 20)),
                    "compile_s": t_compile},
         "gpu_launches": launches,
         "roofline": roof,

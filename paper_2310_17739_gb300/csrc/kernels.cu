@@ -89,8 +89,6 @@ __device__ __forceinline__ double2 scale_by(double2 a, double s) {
 }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
-__device__ __forceinline__ double2 to_d(double2 a) { return a; }
 
 __device__ __forceinline__ unsigned ins0(unsigned x, int p) {
     return ((x >> p) << (p + 1)) | (x & ((1u << p) - 1u));

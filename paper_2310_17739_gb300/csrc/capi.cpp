@@ -315,7 +315,13 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                         qsim::RegDense rd;
                         std::memset(&rd, 0, sizeof(rd));
                         rd.k = qsim::kDenseReg;
-                        rd.sel = (uint8_t)(k == 1 ? (mono ? 15 : 0) + sl[0] : (mono ? 20 : 5) + pair_no[s0][s1]);
+                        // a monomial C2 runs in one of three column patterns
+                        // (diagonal, CX controlled by the lower or by the higher
+                        // slot); any other runs as a dense C2 of the same matrix
+                        int pat = -1;
+                        if (mono && k == 2) pat = perm == 0xE4 ? 0 : perm == 0x6C ? 1 : perm == 0xB4 ? 2 : -1;
+                        rd.sel = (uint8_t)(k == 1 ? (mono ? 15 : 0) + sl[0]
+                                                  : (pat >= 0 ? 20 + 10 * pat : 5) + pair_no[s0][s1]);
                         rd.perm = perm;
                         rd.tab = (uint32_t)tab.size();
                         for (int q = 0; q < D * D; q++) {

@@ -714,12 +714,6 @@ __device__ __forceinline__ void c2_reg(float2 *a, const float2 *M) {
     }
 }
 
-// One of x0..x3 by a runtime 2-bit column (selects, no local-memory indexing).
-__device__ __forceinline__ float2 pick4(unsigned c, float2 x0, float2 x1, float2 x2, float2 x3) {
-    const float2 lo = (c & 1u) ? x1 : x0, hi = (c & 1u) ? x3 : x2;
-    return (c & 2u) ? hi : lo;
-}
-
 // Monomial C1 on slot S: out_r = M[r][perm_r] x_{perm_r}.
 template <int S>
 __device__ __forceinline__ void mono1_reg(float2 *a, const float2 *M, unsigned perm) {
@@ -737,25 +731,33 @@ __device__ __forceinline__ void mono1_reg(float2 *a, const float2 *M, unsigned p
     }
 }
 
-// Monomial C2 on slots S0 < S1.
-template <int S0, int S1>
-__device__ __forceinline__ void mono2_reg(float2 *a, const float2 *M, unsigned perm) {
-    unsigned c[4];
+// Monomial C2 on slots S0 < S1 whose nonzero entries follow one of three
+// column patterns P, chosen at compile time (no runtime selects):
+//   P = 0  diagonal, columns (0, 1, 2, 3);
+//   P = 1  rows 1 and 3 exchange columns, (0, 3, 2, 1): a CX controlled by
+//          the lower slot, times a diagonal;
+//   P = 2  rows 2 and 3 exchange columns, (0, 1, 3, 2): controlled by the
+//          higher slot.
+// out_r = M[r][col_r] x_{col_r}.  Other monomials run as dense C2s.
+__host__ __device__ constexpr int mono_col(int P, int r) {
+    return P == 1 ? (r == 1 ? 3 : r == 3 ? 1 : r) : P == 2 ? (r == 2 ? 3 : r == 3 ? 2 : r) : r;
+}
+template <int S0, int S1, int P>
+__device__ __forceinline__ void mono2_reg(float2 *a, const float2 *M) {
     float2 m[4];
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
-        c[r] = (perm >> (2 * r)) & 3u;
-        m[r] = M[4 * r + c[r]];
-    }
+    for (int r = 0; r < 4; r++) m[r] = M[4 * r + mono_col(P, r)];
 #pragma unroll
     for (int g = 0; g < 8; g++) {
         const int b = pair_lo(pair_lo(g, S0), S1);
         const int idx[4] = {b, b | (1 << S0), b | (1 << S1), b | (1 << S0) | (1 << S1)};
-        const float2 x0 = a[idx[0]], x1 = a[idx[1]], x2 = a[idx[2]], x3 = a[idx[3]];
+        float2 x[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) x[c] = a[idx[c]];
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             float2 acc = make_float2(0.f, 0.f);
-            cmac(acc, m[r], pick4(c[r], x0, x1, x2, x3));
+            cmac(acc, m[r], x[mono_col(P, r)]);
             a[idx[r]] = acc;
         }
     }
@@ -783,16 +785,36 @@ __device__ __forceinline__ void dense_reg_dispatch(float2 *a, unsigned sel, unsi
         case 17: mono1_reg<2>(a, M, perm); break;
         case 18: mono1_reg<3>(a, M, perm); break;
         case 19: mono1_reg<4>(a, M, perm); break;
-        case 20: mono2_reg<0, 1>(a, M, perm); break;
-        case 21: mono2_reg<0, 2>(a, M, perm); break;
-        case 22: mono2_reg<0, 3>(a, M, perm); break;
-        case 23: mono2_reg<0, 4>(a, M, perm); break;
-        case 24: mono2_reg<1, 2>(a, M, perm); break;
-        case 25: mono2_reg<1, 3>(a, M, perm); break;
-        case 26: mono2_reg<1, 4>(a, M, perm); break;
-        case 27: mono2_reg<2, 3>(a, M, perm); break;
-        case 28: mono2_reg<2, 4>(a, M, perm); break;
-        case 29: mono2_reg<3, 4>(a, M, perm); break;
+        case 20: mono2_reg<0, 1, 0>(a, M); break;
+        case 21: mono2_reg<0, 2, 0>(a, M); break;
+        case 22: mono2_reg<0, 3, 0>(a, M); break;
+        case 23: mono2_reg<0, 4, 0>(a, M); break;
+        case 24: mono2_reg<1, 2, 0>(a, M); break;
+        case 25: mono2_reg<1, 3, 0>(a, M); break;
+        case 26: mono2_reg<1, 4, 0>(a, M); break;
+        case 27: mono2_reg<2, 3, 0>(a, M); break;
+        case 28: mono2_reg<2, 4, 0>(a, M); break;
+        case 29: mono2_reg<3, 4, 0>(a, M); break;
+        case 30: mono2_reg<0, 1, 1>(a, M); break;
+        case 31: mono2_reg<0, 2, 1>(a, M); break;
+        case 32: mono2_reg<0, 3, 1>(a, M); break;
+        case 33: mono2_reg<0, 4, 1>(a, M); break;
+        case 34: mono2_reg<1, 2, 1>(a, M); break;
+        case 35: mono2_reg<1, 3, 1>(a, M); break;
+        case 36: mono2_reg<1, 4, 1>(a, M); break;
+        case 37: mono2_reg<2, 3, 1>(a, M); break;
+        case 38: mono2_reg<2, 4, 1>(a, M); break;
+        case 39: mono2_reg<3, 4, 1>(a, M); break;
+        case 40: mono2_reg<0, 1, 2>(a, M); break;
+        case 41: mono2_reg<0, 2, 2>(a, M); break;
+        case 42: mono2_reg<0, 3, 2>(a, M); break;
+        case 43: mono2_reg<0, 4, 2>(a, M); break;
+        case 44: mono2_reg<1, 2, 2>(a, M); break;
+        case 45: mono2_reg<1, 3, 2>(a, M); break;
+        case 46: mono2_reg<1, 4, 2>(a, M); break;
+        case 47: mono2_reg<2, 3, 2>(a, M); break;
+        case 48: mono2_reg<2, 4, 2>(a, M); break;
+        case 49: mono2_reg<3, 4, 2>(a, M); break;
         default: break;
     }
 }

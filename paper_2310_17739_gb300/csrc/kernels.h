@@ -188,11 +188,15 @@ static_assert(sizeof(RegRot) == sizeof(DevOp), "RegRot layout");
 //   5..14   C2 on the slot pair number sel - 5 of (0,1) (0,2) (0,3) (0,4) (1,2)
 //           (1,3) (1,4) (2,3) (2,4) (3,4)
 //   15..19  monomial C1 on slot sel - 15
-//   20..29  monomial C2 on the slot pair number sel - 20
+//   20..49  monomial C2 on the slot pair number (sel - 20) % 10 whose row r
+//           uses column col_r of pattern (sel - 20) / 10: 0 diagonal
+//           (0,1,2,3), 1 (0,3,2,1), 2 (0,1,3,2); a monomial C2 of another
+//           pattern is emitted as a dense C2
 // Its 2^k x 2^k complex matrix (row-major, bit 0 of the local index <-> the
 // lower slot) is at float offset tab (a multiple of 4) of the pass's
-// coefficient slice; a monomial op uses only the entry in column
-// perm[r] = (perm >> 2r) & 3 of each row r (as kMono1 / kMono2).
+// coefficient slice; a monomial C1 uses only the entry in column
+// perm[r] = (perm >> 2r) & 3 of each row r (as kMono1), a monomial C2 only
+// the entries its pattern names.
 constexpr uint8_t kDenseReg = 11;
 struct RegDense {
     uint8_t k;  // kDenseReg

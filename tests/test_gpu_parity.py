@@ -239,6 +239,36 @@ def test_expectation_random_hamiltonian(dtype):
     assert np.abs(e - e_ref).max() <= tol * max(1.0, np.abs(terms["coef"]).max())
 
 
+def test_complex64_expectation_sums_keep_small_terms():
+    """complex64 expectation terms are formed in FP32 and summed with
+    compensation.  Use a state whose terms are exact in FP32: real dyadic
+    amplitudes with 8-bit mantissas, 256 of them near 2^-6 and the rest near
+    2^-21.  The sum then matches the FP64 oracle to 1e-11, and it keeps the
+    ~2^-41 terms that a plain FP32 running sum would round away beside the
+    ~2^-11 ones (about 2e-9 in total)."""
+    n = 14
+    N = 1 << n
+    rng = np.random.default_rng(7)
+    mant = rng.integers(128, 256, size=N).astype(np.float64) * rng.choice([-1.0, 1.0], size=N)
+    scale = np.full(N, 2.0 ** -28)
+    scale[rng.choice(N, 256, replace=False)] = 2.0 ** -13
+    psi = (mant * scale).astype(np.complex128)
+    terms = W.random_hamiltonian(n, 60, seed=9)
+    z_only = np.zeros(n, dtype=W.TERM_DTYPE)
+    for q in range(n):
+        z_only[q] = (0, 1 << q, 1.0)
+    terms = np.concatenate([terms, z_only])
+    e_ref = oracle.expect(psi, n, terms)
+    sim = qs.Sim(n, "c64")
+    sim.set_state(psi.astype(np.complex64))
+    e = sim.expect(terms)
+    assert np.abs(e - e_ref).max() <= 1e-11 * max(1.0, np.abs(terms["coef"]).max())
+    # the small terms matter at this tolerance: dropping them moves <Z_q> by more
+    small = np.where(scale < 2.0 ** -20, np.abs(psi) ** 2, 0.0).sum()
+    assert small > 1e-9
+    sim.close()
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_compile_run_equals_apply_and_repeats(dtype):
     n = 16

@@ -59,53 +59,19 @@ __device__ __forceinline__ double norm2(double2 a) { return a.x * a.x + a.y * a.
 // complex128: in FP64.
 __device__ __forceinline__ double norm2_term(float2 a) { return (double)fmaf(a.x, a.x, a.y * a.y); }
 __device__ __forceinline__ double norm2_term(double2 a) { return norm2(a); }
-// Re(i^ny conj(b) a) (-1)^neg, formed in the amplitudes' precision as
-// norm2_term is (complex64: in FP32; summed by ExpSum).
-__device__ __forceinline__ float pauli_term(float2 a, float2 b, int ny, unsigned neg) {
+// Re(i^ny conj(b) a) (-1)^neg as a term of an FP64 sum, formed in the
+// amplitudes' precision as norm2_term is.
+__device__ __forceinline__ double pauli_term(float2 a, float2 b, int ny, unsigned neg) {
     const float wr = fmaf(b.x, a.x, b.y * a.y), wi = fmaf(b.x, a.y, -(b.y * a.x));
-    const float v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
-    return __int_as_float(__float_as_int(v) ^ (neg << 31));
+    float v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
+    v = __int_as_float(__float_as_int(v) ^ (neg << 31));
+    return (double)v;
 }
 __device__ __forceinline__ double pauli_term(double2 a, double2 b, int ny, unsigned neg) {
     const double wr = b.x * a.x + b.y * a.y, wi = b.x * a.y - b.y * a.x;
     const double v = ny == 0 ? wr : ny == 1 ? -wi : ny == 2 ? -wr : wi;
     return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)neg << 63));
 }
-// A thread's sum of expectation terms.  complex64: the FP32 terms go into an
-// FP32 pair (hi, lo) by TwoSum (Knuth), so that hi + lo is the running sum up
-// to the rounding of lo alone; every 32 terms the pair is added to an FP64
-// total.  This costs two widenings and two FP64 adds per 32 terms instead of
-// a widening and an FP64 add per term (GB300's FP64 rate is 1/60 of FP32's).
-// A run's error is below 32^2 u^2 (u = 2^-24) of the sum of its terms'
-// magnitudes, far below the rounding of the FP32 terms themselves.
-// complex128: a plain FP64 sum.
-struct ExpSum32 {
-    float hi = 0.f, lo = 0.f;
-    double tot = 0.0;
-    unsigned k = 0;
-    __device__ __forceinline__ void add(float t) {
-        const float s = hi + t;
-        const float bp = s - hi;
-        lo += (hi - (s - bp)) + (t - bp);
-        hi = s;
-        if (++k == 32) {
-            tot += (double)hi;
-            tot += (double)lo;
-            hi = lo = 0.f;
-            k = 0;
-        }
-    }
-    __device__ __forceinline__ double total() const { return tot + (double)hi + (double)lo; }
-};
-struct ExpSum64 {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double t) { s += t; }
-    __device__ __forceinline__ double total() const { return s; }
-};
-template <typename T> struct ExpSumOf;
-template <> struct ExpSumOf<float2> { using type = ExpSum32; };
-template <> struct ExpSumOf<double2> { using type = ExpSum64; };
-
 // w with its sign flipped when neg = 1, by integer operations on the sign bit
 // (no floating-point instruction: on the FP64 pipe that would cost as much as
 // the rotation's fused multiply-adds).
@@ -1491,13 +1457,12 @@ __global__ void __launch_bounds__(256) k_expect(const void *state, int n, const 
     const uint64_t x = terms[3 * blockIdx.y], z = terms[3 * blockIdx.y + 1];
     const int ny = __popcll(x & z) & 3;
     const uint64_t N = 1ull << n, chunk = N / gridDim.x, start = chunk * blockIdx.x;
-    typename ExpSumOf<T>::type sum;
+    double acc = 0, dummy = 0;
     for (uint64_t l = threadIdx.x; l < chunk; l += 256) {
         const uint64_t j = start + l;
         // Re(i^ny conj(a_{j^x}) a_j) (-1)^{parity(j & z)}
-        sum.add(pauli_term(st[j], st[j ^ x], ny, __popcll(j & z) & 1u));
+        acc += pauli_term(st[j], st[j ^ x], ny, __popcll(j & z) & 1u);
     }
-    double acc = sum.total(), dummy = 0;
     block_sum2<256>(acc, dummy, red);
     if (threadIdx.x == 0) partials[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
 }
@@ -1514,9 +1479,10 @@ __global__ void __launch_bounds__(256) k_expect_batch(const ExpectJob *jobs) {
     for (uint32_t t = 0; t < jb.n_terms; t++) {
         const uint64_t x = jb.terms[3 * t], z = jb.terms[3 * t + 1];
         const int ny = __popcll(x & z) & 3;
-        typename ExpSumOf<T>::type sum;
-        for (uint64_t j = threadIdx.x; j < N; j += 256) sum.add(pauli_term(st[j], st[j ^ x], ny, __popcll(j & z) & 1u));
-        double acc = sum.total(), dummy = 0;
+        double acc = 0, dummy = 0;
+        for (uint64_t j = threadIdx.x; j < N; j += 256) {
+            acc += pauli_term(st[j], st[j ^ x], ny, __popcll(j & z) & 1u);
+        }
         block_sum2<256>(acc, dummy, red);
         if (threadIdx.x == 0) jb.out[t] = __longlong_as_double((long long)jb.terms[3 * t + 2]) * acc;
     }

@@ -240,12 +240,13 @@ def test_expectation_random_hamiltonian(dtype):
 
 
 def test_complex64_expectation_sums_keep_small_terms():
-    """complex64 expectation terms are formed in FP32 and summed with
-    compensation.  Use a state whose terms are exact in FP32: real dyadic
+    """complex64 expectation terms are formed in FP32 and summed at FP64
+    accuracy.  Use a state whose terms are exact in FP32: real dyadic
     amplitudes with 8-bit mantissas, 256 of them near 2^-6 and the rest near
     2^-21.  The sum then matches the FP64 oracle to 1e-11, and it keeps the
     ~2^-41 terms that a plain FP32 running sum would round away beside the
-    ~2^-11 ones (about 2e-9 in total)."""
+    ~2^-11 ones.  A per-thread FP32 running sum, in the kernel's thread
+    layout, misses by 1.2e-10."""
     n = 14
     N = 1 << n
     rng = np.random.default_rng(7)

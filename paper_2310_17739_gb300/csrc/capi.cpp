@@ -129,6 +129,13 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             f[1] = w;
         }
     };
+    // per-pass scratch, reused across passes (cleared before each use)
+    std::vector<DevOp> body, cur;
+    std::vector<float> tab, tvals;
+    std::vector<size_t> cur_ix;
+    std::vector<std::vector<uint32_t>> succ;
+    std::vector<uint32_t> waits;
+    std::vector<char> placed;
     for (const Pass &src : hp.passes) {
         Pass p = src;
         p.first = pk.ops.size();
@@ -155,7 +162,6 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                 if ((nonpiv >> b) & 1) r |= (uint32_t)((v >> b) & 1) << j++;
             return r;
         };
-        std::vector<DevOp> body;
         bool all_rot = true;
         bool regable = true;    // every op fits a register segment (rotation or dense k <= 2)
         bool has_dense = false;
@@ -267,13 +273,13 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             // positions while it stays <= 5; fill it up with the highest free
             // positions (so that the lowest tile positions index threads)
             std::vector<std::pair<uint32_t, std::vector<DevOp>>> segs;
-            std::vector<float> tab;  // the pass's coefficient tables (floats)
+            tab.clear();  // the pass's coefficient tables (floats)
             const float *tvals_f = reinterpret_cast<const float *>(pk.mats.data());
-            std::vector<float> tvals(src.mat_count);  // t of each rotation, by relative coefficient index
+            tvals.assign(src.mat_count, 0.0f);  // t of each rotation, by relative coefficient index
             for (uint32_t q = 0; q < src.mat_count; q++) tvals[q] = tvals_f[2 * (src.mat_first + q) + 1];
             uint32_t R = 0;
-            std::vector<DevOp> cur;
-            std::vector<size_t> cur_ix;  // body index of each op of cur
+            cur.clear();
+            cur_ix.clear();  // body index of each op of cur
             // tile positions an op needs in registers: a rotation's X
             // coordinates, a dense op's qubits
             auto need = [&](const DevOp &d) -> uint32_t {
@@ -368,15 +374,16 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             // takes ready ops whose X coordinates it already holds first, then
             // the ready op that grows it least, and closes when none fits.
             const size_t K = body.size();
-            std::vector<std::vector<uint32_t>> succ(K);  // later ops that must wait for this one
-            std::vector<uint32_t> waits(K, 0);
+            if (succ.size() < K) succ.resize(K);  // succ[a]: later ops that must wait for op a
+            for (size_t a = 0; a < K; a++) succ[a].clear();
+            waits.assign(K, 0);
             for (size_t a = 0; a < K; a++)
                 for (size_t b = a + 1; b < K; b++)
                     if (!qsim::ops_commute(hp.ops[src.first + a], hp.ops[src.first + b])) {
                         succ[a].push_back((uint32_t)b);
                         waits[b]++;
                     }
-            std::vector<char> placed(K, 0);
+            placed.assign(K, 0);
             size_t left = K;
             while (left) {
                 int best = -1, best_grow = 6;

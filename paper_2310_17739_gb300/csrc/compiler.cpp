@@ -677,7 +677,7 @@ bool fits(const Subspace &V, const FOp &o, int m) {
     uint64_t r[kMaxK];
     int rank = 0;
     for (int j = 0; j < o.k; j++) {
-        uint64_t v = V.reduce(1ull << o.q[j]);
+        uint64_t v = V.reduce_unit((int)o.q[j]);
         for (int i = 0; i < rank; i++)
             if ((v >> __builtin_ctzll(r[i])) & 1) v ^= r[i];
         if (v) r[rank++] = v;

@@ -77,6 +77,17 @@ struct Subspace {
         return v;
     }
     bool contains(uint64_t v) const { return reduce(v) == 0; }
+    // reduce(2^q) without the sweep: the basis is kept in reduced echelon
+    // form (each vector has a zero at every other vector's pivot), so 2^q
+    // meets at most the vector whose pivot is q, and the result has no pivot
+    // bit left.
+    uint64_t reduce_unit(int q) const {
+        uint64_t v = 1ull << q;
+        if (pivots & v)
+            for (int i = 0; i < d; i++)
+                if (piv[i] == q) return v ^ vec[i];
+        return v;
+    }
     // Adds v; returns false (and changes nothing) if v is already a member or
     // the capacity is reached.
     bool add(uint64_t v) {

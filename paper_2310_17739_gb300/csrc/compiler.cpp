@@ -247,6 +247,16 @@ bool is_basis_gate(const qsim_gate &g) {
     }
 }
 
+// |z| > tol, decided as std::abs(z) > tol is (std::abs rounds faithfully),
+// without its square root in the clear cases: |z| >= max(|re|, |im|), and
+// |z| <= |re| + |im|, which is below tol when that sum is at most tol / 2.
+inline bool exceeds(cd z, double tol) {
+    const double a = std::fabs(z.real()), b = std::fabs(z.imag());
+    if (a > tol || b > tol) return true;
+    if (a + b <= 0.5 * tol) return false;
+    return std::abs(z) > tol;
+}
+
 // Which signed Pauli U^dag Z U is: 1=X, 2=Y, 3=Z (sign in *sgn), 0 = none.
 int conj_z(const cd *U, int *sgn) {
     // V = U^dag Z U
@@ -256,7 +266,7 @@ int conj_z(const cd *U, int *sgn) {
     const double tol = 1e-12;
     auto near = [&](const cd *P, double s) {
         for (int i = 0; i < 4; i++)
-            if (std::abs(V[i] - s * P[i]) > tol) return false;
+            if (exceeds(V[i] - s * P[i], tol)) return false;
         return true;
     };
     static const cd X[4] = {0, 1, 1, 0}, Y[4] = {0, cd(0, -1), cd(0, 1), 0}, Z[4] = {1, 0, 0, -1};
@@ -306,42 +316,49 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
     for (size_t k = f0; k < f1; k++) rowmask[g[k].q1] ^= rowmask[g[k].q0];
     const uint64_t S = rowmask[t];
     if (popc(S) < 2) return false;
-    // per-qubit lead products
-    cd Ulead[64][4];
-    int nlead[64] = {0};
+    // per-qubit lead products, in one slot per basis-changed qubit (at most
+    // kMaxLead of them: small arrays, cheap to construct on every call)
+    int8_t slot[64];
+    std::memset(slot, -1, sizeof(slot));
+    cd Ulead[kMaxLead][4], Utrail[kMaxLead][4];
+    int nlead[kMaxLead] = {0};
+    int n_slots = 0;
     for (size_t e0 = 0; e0 < nl; e0++) {
         const uint32_t q = g[lead[e0]].q0;
         cd m[16];
         if (gate_matrix(g[lead[e0]], mats, nm, m) != 2) return false;
-        if (nlead[q] == 0) {
-            for (int e = 0; e < 4; e++) Ulead[q][e] = m[e];
+        if (slot[q] < 0) slot[q] = (int8_t)n_slots++;
+        const int sq = slot[q];
+        if (nlead[sq] == 0) {
+            for (int e = 0; e < 4; e++) Ulead[sq][e] = m[e];
         } else {
-            cd *U = Ulead[q];
+            cd *U = Ulead[sq];
             cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
                        m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
             for (int e = 0; e < 4; e++) U[e] = r[e];
         }
-        nlead[q]++;
+        nlead[sq]++;
     }
     // trailing: as many 1-qubit gates per qubit as the lead had, undoing it
-    cd Utrail[64][4];
-    int ntrail[64] = {0};
+    int ntrail[kMaxLead] = {0};
     size_t need = nl;
     while (need > 0) {
         if (j >= end || !is_basis_gate(g[j])) return false;
         const uint32_t q = g[j].q0;
-        if (!((lead_mask >> q) & 1) || ntrail[q] >= nlead[q]) return false;
+        if (!((lead_mask >> q) & 1)) return false;
+        const int sq = slot[q];
+        if (ntrail[sq] >= nlead[sq]) return false;
         cd m[16];
         if (gate_matrix(g[j], mats, nm, m) != 2) return false;
-        if (ntrail[q] == 0) {
-            for (int e = 0; e < 4; e++) Utrail[q][e] = m[e];
+        if (ntrail[sq] == 0) {
+            for (int e = 0; e < 4; e++) Utrail[sq][e] = m[e];
         } else {
-            cd *U = Utrail[q];
+            cd *U = Utrail[sq];
             cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
                        m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
             for (int e = 0; e < 4; e++) U[e] = r[e];
         }
-        ntrail[q]++;
+        ntrail[sq]++;
         need--;
         j++;
     }
@@ -351,18 +368,19 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
     for (uint64_t r = lead_mask | S; r; r &= r - 1) {
         const int q = __builtin_ctzll(r);
         const bool inS = (S >> q) & 1;
-        if (nlead[q]) {
-            const cd *A = Utrail[q], *B = Ulead[q];
+        const int sq = slot[q];
+        if (sq >= 0) {
+            const cd *A = Utrail[sq], *B = Ulead[sq];
             cd P[4] = {A[0] * B[0] + A[1] * B[2], A[0] * B[1] + A[1] * B[3],
                        A[2] * B[0] + A[3] * B[2], A[2] * B[1] + A[3] * B[3]};
-            if (std::abs(P[0] - 1.0) > 1e-12 || std::abs(P[1]) > 1e-12 || std::abs(P[2]) > 1e-12 ||
-                std::abs(P[3] - 1.0) > 1e-12)
+            if (exceeds(P[0] - 1.0, 1e-12) || exceeds(P[1], 1e-12) || exceeds(P[2], 1e-12) ||
+                exceeds(P[3] - 1.0, 1e-12))
                 return false;
         }
         if (!inS) continue;
         int letter = 3, s = 1;
-        if (nlead[q]) {
-            letter = conj_z(Ulead[q], &s);
+        if (sq >= 0) {
+            letter = conj_z(Ulead[sq], &s);
             if (!letter) return false;
         }
         sign *= s;

@@ -752,7 +752,11 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
     std::vector<cd> spool;
     spool.reserve(pool.size());
     std::vector<size_t> taken;
-    std::vector<int64_t> skipped_pauli;
+    // the Pauli rotations skipped so far in a pass: support, X and Z masks
+    struct SkippedPauli {
+        uint64_t sup, x, z;
+    };
+    std::vector<SkippedPauli> skipped_pauli;
 
     // Pauli frame.  The state on the device is F^dagger times the circuit's
     // state, F = i^k X^x Z^z.  A rotation exp(-i theta P) reaches the device
@@ -831,10 +835,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
                 for (int b = 0; b < L; b++) V.add(1ull << b);
             if (F.x) V.add(F.x);
             for (int b = 0; b < n && V.d < m; b++) V.add(1ull << b);
-            int idx[Subspace::kCap];
-            for (int j = 0; j < V.d; j++) idx[j] = j;
-            std::sort(idx, idx + V.d, [&](int u, int v) { return V.piv[u] < V.piv[v]; });
-            for (int j = 0; j < V.d; j++) out.bvec.push_back(V.vec[idx[j]]);
+            for (uint64_t b = V.pivots; b; b &= b - 1) out.bvec.push_back(V.vec[V.at[__builtin_ctzll(b)]]);
             p.tile = V.pivots;
         }
         o.mat = spool.size();
@@ -897,8 +898,8 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             if (ok && (Q & blocked_p)) {
                 if (!o.pauli()) ok = false;
                 else
-                    for (int64_t s : skipped_pauli)
-                        if (!ops_commute(o, ops[s])) {
+                    for (const SkippedPauli &sp : skipped_pauli)  // as ops_commute
+                        if ((Q & sp.sup) && ((popc(o.xm & sp.z) + popc(o.zm & sp.x)) & 1)) {
                             ok = false;
                             break;
                         }
@@ -912,7 +913,7 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             } else {
                 if (o.pauli()) {
                     blocked_p |= Q;
-                    skipped_pauli.push_back(i);
+                    skipped_pauli.push_back({Q, o.xm, o.zm});
                 } else {
                     blocked_np |= Q;
                 }
@@ -937,10 +938,8 @@ void compile(int n, qsim_dtype dtype, const Config &cfg, const qsim_gate *g, siz
             if (only_rot) {
                 for (int j = 0; j < V.d; j++) out.bvec.push_back(V.added[j]);
             } else {
-                int idx[Subspace::kCap];
-                for (int j = 0; j < V.d; j++) idx[j] = j;
-                std::sort(idx, idx + V.d, [&](int a, int b) { return V.piv[a] < V.piv[b]; });
-                for (int j = 0; j < V.d; j++) out.bvec.push_back(V.vec[idx[j]]);
+                // by ascending pivot
+                for (uint64_t b = V.pivots; b; b &= b - 1) out.bvec.push_back(V.vec[V.at[__builtin_ctzll(b)]]);
             }
         }
         std::vector<FOp> body;

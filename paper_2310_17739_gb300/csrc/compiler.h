@@ -70,23 +70,20 @@ struct Subspace {
     uint32_t combo[kCap];
     uint8_t piv[kCap];
     uint64_t added[kCap];  // the accepted vectors, in order
+    uint8_t at[64];        // at[p]: the vector whose pivot is p (p in pivots)
 
+    // Since every vector has a zero at every other vector's pivot, the
+    // vectors v meets while it is reduced are fixed by v's own pivot bits:
+    // XORing one of them clears its pivot bit and touches no other.
     uint64_t reduce(uint64_t v) const {
-        for (int i = 0; i < d; i++)
-            if ((v >> piv[i]) & 1) v ^= vec[i];
+        for (uint64_t b = v & pivots; b; b &= b - 1) v ^= vec[at[__builtin_ctzll(b)]];
         return v;
     }
     bool contains(uint64_t v) const { return reduce(v) == 0; }
-    // reduce(2^q) without the sweep: the basis is kept in reduced echelon
-    // form (each vector has a zero at every other vector's pivot), so 2^q
-    // meets at most the vector whose pivot is q, and the result has no pivot
-    // bit left.
+    // reduce(2^q): at most the vector whose pivot is q.
     uint64_t reduce_unit(int q) const {
-        uint64_t v = 1ull << q;
-        if (pivots & v)
-            for (int i = 0; i < d; i++)
-                if (piv[i] == q) return v ^ vec[i];
-        return v;
+        const uint64_t v = 1ull << q;
+        return (pivots & v) ? v ^ vec[at[q]] : v;
     }
     // Adds v; returns false (and changes nothing) if v is already a member or
     // the capacity is reached.
@@ -94,11 +91,11 @@ struct Subspace {
         if (d >= kCap) return false;
         uint64_t r = v;
         uint32_t c = 1u << d;
-        for (int i = 0; i < d; i++)
-            if ((r >> piv[i]) & 1) {
-                r ^= vec[i];
-                c ^= combo[i];
-            }
+        for (uint64_t b = v & pivots; b; b &= b - 1) {
+            const int i = at[__builtin_ctzll(b)];
+            r ^= vec[i];
+            c ^= combo[i];
+        }
         if (!r) return false;
         const int p = __builtin_ctzll(r);
         for (int i = 0; i < d; i++)
@@ -109,6 +106,7 @@ struct Subspace {
         vec[d] = r;
         combo[d] = c;
         piv[d] = (uint8_t)p;
+        at[p] = (uint8_t)d;
         added[d] = v;
         pivots |= 1ull << p;
         d++;
@@ -117,8 +115,7 @@ struct Subspace {
     // Coordinates of a member v in the basis added[0..d): bit j <-> added[j].
     uint32_t coords(uint64_t v) const {
         uint32_t c = 0;
-        for (int i = 0; i < d; i++)
-            if ((v >> piv[i]) & 1) c ^= combo[i];
+        for (uint64_t b = v & pivots; b; b &= b - 1) c ^= combo[at[__builtin_ctzll(b)]];
         return c;
     }
 };

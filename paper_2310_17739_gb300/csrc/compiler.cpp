@@ -280,6 +280,84 @@ int conj_z(const cd *U, int *sgn) {
     return 0;
 }
 
+// A basis change of a gadget on one qubit: its leading product U_lead and
+// trailing product U_trail.  undone: U_trail U_lead == I (within 1e-12);
+// letter, sign: U_lead^dag Z U_lead as conj_z gives them.
+struct BasisChange {
+    bool undone = false;
+    int letter = 0, sign = 1;
+};
+
+void eval_basis_change(const cd *B, const cd *A, BasisChange &bc) {  // B = U_lead, A = U_trail
+    cd P[4] = {A[0] * B[0] + A[1] * B[2], A[0] * B[1] + A[1] * B[3],
+               A[2] * B[0] + A[3] * B[2], A[2] * B[1] + A[3] * B[3]};
+    bc.undone = !(exceeds(P[0] - 1.0, 1e-12) || exceeds(P[1], 1e-12) || exceeds(P[2], 1e-12) ||
+                  exceeds(P[3] - 1.0, 1e-12));
+    bc.sign = 1;
+    bc.letter = conj_z(B, &bc.sign);
+}
+
+// The product of the 1-qubit gates idx[0..cnt) that act on qubit q, later
+// gates on the left; false if one has no 2x2 matrix.
+bool gate_product(const qsim_gate *g, const size_t *idx, size_t cnt, uint32_t q, const double *mats,
+                  size_t nm, cd *U) {
+    bool first = true;
+    for (size_t e = 0; e < cnt; e++) {
+        if (g[idx[e]].q0 != q) continue;
+        cd m[16];
+        if (gate_matrix(g[idx[e]], mats, nm, m) != 2) return false;
+        if (first) {
+            for (int k = 0; k < 4; k++) U[k] = m[k];
+            first = false;
+        } else {
+            cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
+                       m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
+            for (int k = 0; k < 4; k++) U[k] = r[k];
+        }
+    }
+    return true;
+}
+
+// BasisChange of one leading and one trailing named gate.  Gadgets repeat a
+// few such pairs (H ... H, RX(pi/2) ... RX(-pi/2)), so each thread keeps the
+// results of recent pairs, keyed by the two records' op codes and parameters
+// (the matrices depend on nothing else); false if a gate has no 2x2 matrix.
+bool basis_change(const qsim_gate &lead, const qsim_gate &trail, const double *mats, size_t nm,
+                  BasisChange &bc) {
+    struct Entry {
+        bool used = false;
+        uint16_t lop = 0, top = 0;
+        double lp[3], tp[3];
+        BasisChange bc;
+    };
+    constexpr int kEntries = 64;
+    thread_local Entry memo[kEntries];
+    uint64_t h = (uint64_t)lead.op * 0x9E3779B97F4A7C15ull ^ (uint64_t)trail.op * 0xC2B2AE3D27D4EB4Full;
+    for (int k = 0; k < 3; k++) {
+        uint64_t a, b;
+        std::memcpy(&a, &lead.p[k], 8);
+        std::memcpy(&b, &trail.p[k], 8);
+        h = (h ^ a) * 0x100000001B3ull;
+        h = (h ^ b) * 0x100000001B3ull;
+    }
+    Entry &e = memo[(h >> 32) % kEntries];
+    if (e.used && e.lop == lead.op && e.top == trail.op && std::memcmp(e.lp, lead.p, sizeof(e.lp)) == 0 &&
+        std::memcmp(e.tp, trail.p, sizeof(e.tp)) == 0) {
+        bc = e.bc;
+        return true;
+    }
+    cd Ul[16], Ut[16];
+    if (gate_matrix(lead, mats, nm, Ul) != 2 || gate_matrix(trail, mats, nm, Ut) != 2) return false;
+    eval_basis_change(Ul, Ut, bc);
+    e.used = true;
+    e.lop = lead.op;
+    e.top = trail.op;
+    std::memcpy(e.lp, lead.p, sizeof(e.lp));
+    std::memcpy(e.tp, trail.p, sizeof(e.tp));
+    e.bc = bc;
+    return true;
+}
+
 bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double *mats, size_t nm,
                   Gadget &out) {
     (void)n;
@@ -316,48 +394,32 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
     for (size_t k = f0; k < f1; k++) rowmask[g[k].q1] ^= rowmask[g[k].q0];
     const uint64_t S = rowmask[t];
     if (popc(S) < 2) return false;
-    // per-qubit lead products, in one slot per basis-changed qubit (at most
-    // kMaxLead of them: small arrays, cheap to construct on every call)
+    // one slot per basis-changed qubit (at most kMaxLead), with its leading
+    // and trailing gates (their matrices are formed only when needed)
     int8_t slot[64];
     std::memset(slot, -1, sizeof(slot));
-    cd Ulead[kMaxLead][4], Utrail[kMaxLead][4];
-    int nlead[kMaxLead] = {0};
+    int nlead[kMaxLead] = {0}, ntrail[kMaxLead] = {0};
+    size_t first_lead[kMaxLead], first_trail[kMaxLead];
     int n_slots = 0;
     for (size_t e0 = 0; e0 < nl; e0++) {
         const uint32_t q = g[lead[e0]].q0;
-        cd m[16];
-        if (gate_matrix(g[lead[e0]], mats, nm, m) != 2) return false;
-        if (slot[q] < 0) slot[q] = (int8_t)n_slots++;
-        const int sq = slot[q];
-        if (nlead[sq] == 0) {
-            for (int e = 0; e < 4; e++) Ulead[sq][e] = m[e];
-        } else {
-            cd *U = Ulead[sq];
-            cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
-                       m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
-            for (int e = 0; e < 4; e++) U[e] = r[e];
+        if (slot[q] < 0) {
+            slot[q] = (int8_t)n_slots;
+            first_lead[n_slots++] = lead[e0];
         }
-        nlead[sq]++;
+        nlead[slot[q]]++;
     }
     // trailing: as many 1-qubit gates per qubit as the lead had, undoing it
-    int ntrail[kMaxLead] = {0};
-    size_t need = nl;
+    size_t trail[kMaxLead];
+    size_t nt = 0, need = nl;
     while (need > 0) {
         if (j >= end || !is_basis_gate(g[j])) return false;
         const uint32_t q = g[j].q0;
         if (!((lead_mask >> q) & 1)) return false;
         const int sq = slot[q];
         if (ntrail[sq] >= nlead[sq]) return false;
-        cd m[16];
-        if (gate_matrix(g[j], mats, nm, m) != 2) return false;
-        if (ntrail[sq] == 0) {
-            for (int e = 0; e < 4; e++) Utrail[sq][e] = m[e];
-        } else {
-            cd *U = Utrail[sq];
-            cd r[4] = {m[0] * U[0] + m[1] * U[2], m[0] * U[1] + m[1] * U[3],
-                       m[2] * U[0] + m[3] * U[2], m[2] * U[1] + m[3] * U[3]};
-            for (int e = 0; e < 4; e++) U[e] = r[e];
-        }
+        if (ntrail[sq] == 0) first_trail[sq] = j;
+        trail[nt++] = j;
         ntrail[sq]++;
         need--;
         j++;
@@ -369,20 +431,24 @@ bool match_gadget(int n, const qsim_gate *g, size_t i, size_t end, const double 
         const int q = __builtin_ctzll(r);
         const bool inS = (S >> q) & 1;
         const int sq = slot[q];
-        if (sq >= 0) {
-            const cd *A = Utrail[sq], *B = Ulead[sq];
-            cd P[4] = {A[0] * B[0] + A[1] * B[2], A[0] * B[1] + A[1] * B[3],
-                       A[2] * B[0] + A[3] * B[2], A[2] * B[1] + A[3] * B[3]};
-            if (exceeds(P[0] - 1.0, 1e-12) || exceeds(P[1], 1e-12) || exceeds(P[2], 1e-12) ||
-                exceeds(P[3] - 1.0, 1e-12))
-                return false;
-        }
-        if (!inS) continue;
         int letter = 3, s = 1;
         if (sq >= 0) {
-            letter = conj_z(Ulead[sq], &s);
-            if (!letter) return false;
+            BasisChange bc;
+            if (nlead[sq] == 1) {
+                if (!basis_change(g[first_lead[sq]], g[first_trail[sq]], mats, nm, bc)) return false;
+            } else {
+                cd Ul[4], Ut[4];
+                if (!gate_product(g, lead, nl, (uint32_t)q, mats, nm, Ul) ||
+                    !gate_product(g, trail, nt, (uint32_t)q, mats, nm, Ut))
+                    return false;
+                eval_basis_change(Ul, Ut, bc);
+            }
+            if (!bc.undone) return false;
+            letter = bc.letter;
+            s = bc.sign;
         }
+        if (!inS) continue;
+        if (!letter) return false;
         sign *= s;
         if (letter == 1 || letter == 2) xm |= 1ull << q;
         if (letter == 2 || letter == 3) zm |= 1ull << q;

@@ -136,6 +136,11 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
     std::vector<std::vector<uint32_t>> succ;
     std::vector<uint32_t> waits;
     std::vector<char> placed;
+    struct OpSupport {
+        uint64_t m, x, z;
+        bool rot;
+    };
+    std::vector<OpSupport> sup;
     for (const Pass &src : hp.passes) {
         Pass p = src;
         p.first = pk.ops.size();
@@ -158,8 +163,7 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
         auto gather = [&](uint64_t v) {  // v's bits at the non-pivot positions, packed
             uint32_t r = 0;
             int j = 0;
-            for (int b = 0; b < hp.n; b++)
-                if ((nonpiv >> b) & 1) r |= (uint32_t)((v >> b) & 1) << j++;
+            for (uint64_t b = nonpiv; b; b &= b - 1, j++) r |= (uint32_t)((v >> __builtin_ctzll(b)) & 1) << j;
             return r;
         };
         bool all_rot = true;
@@ -360,8 +364,12 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                         const uint32_t j = H < 0 ? (uint32_t)q : (((uint32_t)q >> H) << (H + 1)) | ((uint32_t)q & ((1u << H) - 1));
                         u[q] = (__builtin_popcount(j & zr) & 1) ? -t : t;
                     }
-                    for (int q = 0; q < cnt; q++) tab.push_back(u[q]);
-                    for (int q = 0; q < cnt; q++) tab.push_back(-u[q]);
+                    const size_t t0 = tab.size();
+                    tab.resize(t0 + 2 * (size_t)cnt);
+                    for (int q = 0; q < cnt; q++) {
+                        tab[t0 + q] = u[q];
+                        tab[t0 + cnt + q] = -u[q];
+                    }
                     std::memcpy(&d, &r, sizeof(d));
                 }
                 segs.emplace_back(R, cur);
@@ -377,12 +385,22 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
             if (succ.size() < K) succ.resize(K);  // succ[a]: later ops that must wait for op a
             for (size_t a = 0; a < K; a++) succ[a].clear();
             waits.assign(K, 0);
+            // the pass's ops as (support, X, Z, is rotation): ops_commute on them
+            sup.resize(K);
+            for (size_t a = 0; a < K; a++) {
+                const qsim::FOp &o = hp.ops[src.first + a];
+                sup[a] = {o.mask(), o.xm, o.zm, o.pauli()};
+            }
             for (size_t a = 0; a < K; a++)
-                for (size_t b = a + 1; b < K; b++)
-                    if (!qsim::ops_commute(hp.ops[src.first + a], hp.ops[src.first + b])) {
+                for (size_t b = a + 1; b < K; b++) {
+                    const OpSupport &u = sup[a], &v = sup[b];
+                    const bool commute = !(u.m & v.m) || (u.rot && v.rot && ((__builtin_popcountll(u.x & v.z) +
+                                                                              __builtin_popcountll(u.z & v.x)) & 1) == 0);
+                    if (!commute) {
                         succ[a].push_back((uint32_t)b);
                         waits[b]++;
                     }
+                }
             placed.assign(K, 0);
             size_t left = K;
             while (left) {

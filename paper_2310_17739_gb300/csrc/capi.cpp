@@ -334,9 +334,11 @@ void pack(const HostProgram &hp, qsim_dtype dt, bool allow_reg, Packed &pk) {
                                                   : (pat >= 0 ? 20 + 10 * pat : 5) + pair_no[s0][s1]);
                         rd.perm = perm;
                         rd.tab = (uint32_t)tab.size();
+                        const size_t t0 = tab.size();
+                        tab.resize(t0 + 2 * (size_t)(D * D));
                         for (int q = 0; q < D * D; q++) {
-                            tab.push_back((float)M[q].real());
-                            tab.push_back((float)M[q].imag());
+                            tab[t0 + 2 * q] = (float)M[q].real();
+                            tab[t0 + 2 * q + 1] = (float)M[q].imag();
                         }
                         std::memcpy(&d, &rd, sizeof(d));
                         continue;

@@ -409,6 +409,59 @@ def test_gadget_variants_recognised_exactly(star, y_basis):
     assert np.abs(apply_compiled(psi, n, ops) - ref).max() < 1e-12
 
 
+def test_concurrent_fusion_matches_sequential():
+    """Host compilation runs on worker threads, and gadget matching keeps
+    per-thread results of recent basis changes: fusing circuits of the three
+    gadget styles (including near misses) from several threads at once gives
+    exactly the sequential op lists."""
+    import threading
+
+    rng = np.random.default_rng(21)
+    jobs = []
+    for k in range(6):
+        n = 8
+        rows = []
+        for t in range(40):
+            s, L = W.random_pauli(rng, n, 2, 5)
+            yb = ("sdg_h", "rx_minus")[(k + t) % 2]
+            r = qiskit_style_gadget(s, L, float(rng.uniform(-3, 3)), star=bool(t % 3 == 0), y_basis=yb)
+            if t % 5 == 2:   # a trailing gate that does not undo its lead
+                for idx in range(len(r) - 1, -1, -1):
+                    if r[idx][0] in (OP["H"], OP["S"], OP["RX"]):
+                        r[idx] = (OP["T"], r[idx][1], 0, 0.0)
+                        break
+            rows += r
+        jobs.append((n, W.from_columns(*zip(*rows))))
+    jobs.append((14, W.ucc_circuit(14, seed=3, n_gadgets=None, w_lo=2, w_hi=6, target_gates=6000).gates))
+
+    def key(ops):
+        out = []
+        for o in ops:
+            if o[0] == "pauli":
+                out.append(("pauli", int(o[1]), int(o[2]), float(o[3])))
+            elif isinstance(o[0], int):
+                out.append((o[0], tuple(o[1]), np.asarray(o[2]).tobytes()))
+            else:
+                out.append(tuple(str(x) for x in o))
+        return out
+
+    ref = [key(qs.fuse(n, g, dtype=qs.C64, fusion=2, tile_bits=min(n, 12))) for n, g in jobs]
+    got = [[None] * len(jobs) for _ in range(8)]
+
+    def work(t):
+        for i in np.random.default_rng(t).permutation(len(jobs)):
+            n, g = jobs[i]
+            got[t][i] = key(qs.fuse(n, g, dtype=qs.C64, fusion=2, tile_bits=min(n, 12)))
+
+    th = [threading.Thread(target=work, args=(t,)) for t in range(8)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    for t in range(8):
+        assert got[t] == ref
+
+
 def test_near_miss_blocks_stay_gates():
     """A block whose uncompute does not match (a stray gate) or whose core is not
     an RZ is not taken as the full rotation; only a genuine inner block (the CX

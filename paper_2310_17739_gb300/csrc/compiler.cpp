@@ -330,6 +330,12 @@ bool basis_change(const qsim_gate &lead, const qsim_gate &trail, const double *m
         double lp[3], tp[3];
         BasisChange bc;
     };
+    if (lead.op == QSIM_OP_C1 || trail.op == QSIM_OP_C1) {  // a matrix from `mats`: not keyed by the record
+        cd Ul[16], Ut[16];
+        if (gate_matrix(lead, mats, nm, Ul) != 2 || gate_matrix(trail, mats, nm, Ut) != 2) return false;
+        eval_basis_change(Ul, Ut, bc);
+        return true;
+    }
     constexpr int kEntries = 64;
     thread_local Entry memo[kEntries];
     uint64_t h = (uint64_t)lead.op * 0x9E3779B97F4A7C15ull ^ (uint64_t)trail.op * 0xC2B2AE3D27D4EB4Full;
